@@ -1,0 +1,347 @@
+"""Benchmark of the EFGP hot path on GB300.
+
+One step = the whole path on one synthetic problem: bin sort + type-1 spread
++ fine FFT + Toeplitz transform (set-up), the CG solve with the FFT Toeplitz
+product, and the type-2 evaluation of the posterior mean at the targets.
+Default workload: 2D Matern-3/2, l = 0.05, sigma = 0.5, eps = 1e-3,
+N = 10^9 points (float32), 1000^2 grid targets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
+own independent problem (weak scaling, no collective on the data path);
+value = all ranks' points / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthdata  # noqa: E402
+
+METRIC = "points/s end-to-end EFGP at stated mean error; spread/interp GB/s vs HBM peak"
+UNIT = "points/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def workload_desc(name, rec, model):
+    fam, nu, ell, sigma, eps = model
+    kern = "SE" if fam == "se" else f"Matern-{nu:g}"
+    tg = f"{rec.n_targets_1d}^{rec.d} grid" if rec.targets == "grid" else f"{rec.n_targets} iid"
+    return f"{name}: {rec.d}D {kern} l={ell} sigma={sigma} eps={eps} N={rec.n} targets {tg}"
+
+
+def n_targets(rec):
+    return rec.n_targets_1d ** rec.d if rec.targets == "grid" else rec.n_targets
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(name, n_sample, q_sample):
+    """The FP64 oracle (direct sums + dense Cholesky + direct evaluation) on a
+    bounded sample of the workload: the first n_sample points and q_sample
+    targets, same kernel and tolerance (hence the same h and m)."""
+    from oracle import efgp_oracle as O
+    rec = synthdata.config(name, n=n_sample)
+    x, y, z = synthdata.make_np(rec)
+    z = z[:q_sample]
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    t0 = time.perf_counter()
+    O.efgp(x, y, z, O.Kernel(fam, nu, ell), sigma, eps)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def cpu_sample_size(name):
+    return {"se1d": 10_000, "matern2d": 200_000, "se3d": 20_000, "matern2d_1e9": 500_000,
+            "matern2d_table4": 50_000}.get(name, 100_000)
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the oracle on the host cores, a bounded sample per step."""
+    if rank != 0:
+        return
+    ns = cpu_sample_size(args.config)
+    qs = 10_000
+    for _ in range(args.warmup):
+        oracle_sample(args.config, max(ns // 10, 1000), 1000)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt = oracle_sample(args.config, ns, qs)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.median(vals)
+    rec = synthdata.config(args.config)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.config, rec, synthdata.MODELS[args.config])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {ns} points of the workload, {qs} targets, same h and m"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args, rank, world):
+    import torch
+    import paper_2210_10210_gb300 as E
+    from paper_2210_10210_gb300 import build
+    build.build()
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    name = args.config
+    rec = synthdata.config(name, n=args.n)
+    rec.seed += 1000 * rank                  # independent problem per rank
+    model = synthdata.MODELS[name]
+    fam, nu, ell, sigma, eps = model
+    kern = E.Kernel(fam, nu, ell)
+    prec = args.precision or ("fp64" if name == "se1d" else "mixed")
+
+    x, y = synthdata.make_torch(rec, dev)
+    z = torch.from_numpy(synthdata.targets_np(rec)).to(dev)
+    q = z.shape[0]
+    torch.cuda.synchronize()
+
+    def step(profile=0):
+        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile)
+        info = h.solve()
+        mu = h.predict(z)
+        pt = h.phase_times()
+        par = h.params()
+        h.close()
+        return info, mu, pt, par
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos, pts = [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            info, mu, pt, par = step(profile=1)
+            infos.append(info)
+            pts.append(pt)
+        ev1.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * rec.n / (ms_step / 1000.0)
+
+    # phase shares and the dominant kernel's roofline
+    keys = ["bin_count_ms", "bin_scatter_ms", "spread_ms", "fine_fft_ms", "what_ms", "cg_ms", "predict_fft_ms",
+            "interp_ms"]
+    tot = {k: sum(p[k] for p in pts) / args.steps for k in keys}
+    launches = sum(p["launches"] for p in pts)
+    iters = [i["iters"] for i in infos]
+    hbm, src = _peaks()
+    d = rec.d
+    rec_bytes = 4 if prec == "mixed" else 8
+    coord_b = 4 if rec.coord_dtype == "float32" else 8
+    val_b = 4 if rec.value_dtype == "float32" else 8
+    # algorithmic bytes: each kernel must read its points (and the count/scatter
+    # write the sorted copy); reported against the kernel's own time
+    alg = {
+        "bin_count_ms": rec.n * d * coord_b,
+        "bin_scatter_ms": rec.n * (d * coord_b + val_b) + rec.n * (d + 1) * rec_bytes,
+        "spread_ms": rec.n * (d + 1) * rec_bytes,
+        "interp_ms": q * (d * coord_b + val_b),
+    }
+    dom = max(keys, key=lambda k: tot[k])
+    roof_kernel = dom if dom in alg else max(alg, key=lambda k: tot[k])
+    kt = tot[roof_kernel]
+    achieved = alg[roof_kernel] / (kt / 1000.0) / 1e9 if kt > 0 else None
+    traffic = None
+    if args.traffic_json and os.path.exists(args.traffic_json):
+        try:
+            traffic = json.load(open(args.traffic_json)).get(roof_kernel)
+        except Exception:
+            traffic = None
+    roofline = {"kernel": roof_kernel.replace("_ms", ""), "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                "peak_source": src, "alg_bytes_per_launch": alg[roof_kernel], "ms_per_launch": kt}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        yh = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+        zh = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
+        xh.copy_(x)
+        yh.copy_(y)
+        zh.copy_(z)
+        xn, yn, zn = xh.numpy(), yh.numpy(), zh.numpy()
+        mu_h = torch.empty(q, dtype=torch.float32 if rec.value_dtype == "float32" else torch.float64,
+                           pin_memory=True).numpy()
+        del x, y
+        torch.cuda.empty_cache()
+
+        def e2e_step():
+            h = E.setup(xn, yn, kern, sigma, eps, precision=prec)
+            h.solve()
+            h.predict(zn, out=mu_h)
+            h.close()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ke
+        if dist:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * rec.n / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes + zn.nbytes), "d2h_bytes_per_step": int(mu_h.nbytes),
+               "ms_per_step": 1000 * te}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns = cpu_sample_size(name)
+        v, dt = oracle_sample(name, ns, 10_000)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {ns} points of the workload, 10000 targets, same h and m ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(name, rec, model), "precision": prec, "m": par["m"],
+                       "M": par["M"], "L": par["L"], "nf1": par["nf1"], "w1": par["w1"], "nf2": par["nf2"],
+                       "w2": par["w2"], "l2_flush": "inputs larger than L2 (%.1f GB)" % (
+                           rec.n * (d * coord_b + val_b) / 1e9), "parallelism": f"independent problem per GPU x{world}"},
+            "cg_iters": iters, "cg_rel_residual": [i["rel_residual"] for i in infos],
+            "phase_ms": {k.replace("_ms", ""): round(v, 4) for k, v in tot.items()},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="matern2d_1e9")
+    ap.add_argument("--n", type=int, default=None, help="override the point count")
+    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "traffic.json"))
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

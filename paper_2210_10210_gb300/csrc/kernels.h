@@ -1,0 +1,86 @@
+// Host-callable launchers of the CUDA kernels of libefgp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace efgp {
+
+// Arguments of the CG-aware first (prologue) and last (epilogue) passes of
+// the Toeplitz matrix-vector product.
+struct CgArgs {
+  double2* src;          // vector the operator is applied to (p in CG)
+  const double2* r;      // residual (for the p update)
+  const double* Dw;      // spectral weights D (M)
+  double2* dst;          // output (A src)
+  double sigma2;         // sigma^2
+  CgState* st;           // CG scalars (may be null outside CG)
+  double* partials;      // per-block partial dot products
+  int update_p;          // 1: first pass sets src = r + beta*src (iteration > 0)
+  int do_dot;            // 1: last pass reduces Re(src^H dst) into st->pAp, alpha
+  int check_done;        // 1: skip everything once st->done is set
+};
+
+enum LineIn { IN_PLAIN = 0, IN_CG = 1 };
+enum LineOut { OUT_PLAIN = 0, OUT_CG = 1 };
+
+// One batched pass of length-L FFTs along one axis (see LineGeom).  dir = -1
+// forward, +1 inverse (unnormalised).  With what != nullptr the pass is a
+// forward FFT, a pointwise product with the real array what (index
+// (o*L + k)*inner + i) and an inverse FFT.
+template <typename T>
+cudaError_t launch_line_fft(const LineGeom& g, const void* in, void* out, int dir, const cplx<T>* tw, const T* what,
+                            int inm, int outm, const CgArgs* cga, int threads, cudaStream_t s);
+
+size_t line_fft_smem_bytes(int L, int nb, size_t elem_bytes);
+constexpr int kLineFftMaxSmem = 200 * 1024;   // dynamic shared memory cap of one pass
+template <typename T>
+cudaError_t prepare_line_fft();
+
+// ---- CG vector kernels (cg.cu)
+cudaError_t launch_cg_init(const double2* b, double2* x, double2* r, double2* p, long long M, double rho,
+                           long long max_iter, CgState* st, double* partials, cudaStream_t s);
+cudaError_t launch_cg_update(double2* x, double2* r, const double2* p, const double2* Ap, long long M, CgState* st,
+                             double* partials, cudaStream_t s);
+cudaError_t launch_residual_norm(const double2* b, const double2* Ax, long long M, double* out_sum, double* partials,
+                                 unsigned int* ticket, cudaStream_t s);
+int cg_blocks(long long M);
+
+// ---- setup kernels (spread.cu and friends)
+struct SortGeom {
+  GridScale gs;
+  int d;
+  int W;
+  int off;          // extended-grid offset
+  int TB;           // tile edge
+  int nt[3];        // tiles per dim
+  int ntiles;
+  int nEx;          // extended grid per dim (nt*TB + W - 1)
+};
+
+cudaError_t launch_bin_count(const void* x, int coord_f64, int rec_f64, int soa, long long N, const SortGeom& sg,
+                             unsigned int* counts, int* range_flag, cudaStream_t s);
+cudaError_t launch_scan_tiles(const unsigned int* counts, int ntiles, long long* tile_off, long long* cursor,
+                              cudaStream_t s);
+cudaError_t launch_bin_scatter(const void* x, int coord_f64, const void* y, int value_f64, int soa, long long N,
+                               const SortGeom& sg, int rec_f64, long long* cursor, void* rec, cudaStream_t s);
+cudaError_t launch_spread(const void* rec, int rec_f64, long long N, const SortGeom& sg, const long long* tile_off,
+                          const void* coef, double2* E, cudaStream_t s);
+cudaError_t launch_spectral_weights(double* Dw, int m, int d, double h, const efgp_kernel& k, cudaStream_t s);
+cudaError_t launch_fold(const double2* E, int nEx, int off, int nf, int d, void* P, int p_f64, cudaStream_t s);
+cudaError_t launch_deconv_split(const void* Phat, int p_f64, int nf, int d, int m, const double* corr1,
+                                const double* Dw, double2* w, double2* b, cudaStream_t s);
+cudaError_t launch_place_w(const double2* w, int m, int d, int L, double2* grid, cudaStream_t s);
+cudaError_t launch_extract_what(const double2* grid, long long n, double scale, void* what, int what_f64,
+                                cudaStream_t s);
+
+// ---- predict kernels (interp.cu)
+cudaError_t launch_precorrect(const double2* beta, const double* Dw, const double* corr2, int m, int d, int nf,
+                              void* g, int g_f64, cudaStream_t s);
+cudaError_t launch_unfold(const void* g, int g_f64, int nf, int d, int off, int nE, void* E2, cudaStream_t s);
+cudaError_t launch_interp(const void* targets, int coord_f64, int soa, long long q, int d, int W, const GridScale& gs,
+                          int off, int nE, const void* E2, int g_f64, const void* coef, void* mu, int value_f64,
+                          int* range_flag, cudaStream_t s);
+
+}  // namespace efgp

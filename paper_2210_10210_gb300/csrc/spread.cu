@@ -1,0 +1,870 @@
+// Setup kernels (Algorithm steps 2-3): bin sort of the points by spread
+// tile, type-1 spreading with the exponential-of-semicircle kernel into
+// shared-memory tiles flushed once per tile visit, folding of the extended
+// grid onto the periodic fine grid, and deconvolution that splits the packed
+// strengths (1 + i y) into the Toeplitz generating vector w (eq. 88, as
+// w = conj v) and the right-hand side D F^* y (eq. rhs).
+#include <cmath>
+#include <cstdio>
+#include <type_traits>
+
+#include "kernels.h"
+
+namespace efgp {
+
+constexpr int kSortThreads = 256;
+constexpr int kScatterPPT = 8;        // points per thread per scatter chunk
+constexpr int kSmemBins = 8192;       // tiles handled with shared-memory histograms
+
+// ---------------------------------------------------------------- tile map
+template <int D, typename TC, typename TR>
+__device__ __forceinline__ int tile_of(const TC* __restrict__ x, int soa, long long N, long long n, const SortGeom& sg,
+                                       TR (&q)[3], bool& bad) {
+  int tc[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    TC xa = soa ? x[(long long)a * N + n] : x[n * D + a];
+    if (!(xa >= TC(0) && xa <= TC(1))) {  // also catches NaN
+      bad = true;
+      xa = TC(0);
+    }
+    int l0;
+    TR f;
+    GridPos<TC, TR>::get(xa, sg.gs, l0, f);
+    int e0 = l0 + sg.off;
+    e0 = max(0, min(e0, sg.nt[a] * sg.TB - 1));
+    tc[a] = e0 / sg.TB;
+    q[a] = (TR)(e0 - tc[a] * sg.TB) + f;   // tile-local footprint start + offset
+  }
+  int t = tc[0];
+  if (D > 1) t = t * sg.nt[1] + tc[1];
+  if (D > 2) t = t * sg.nt[2] + tc[2];
+  return t;
+}
+
+template <int D, typename TC, typename TR>
+__global__ void __launch_bounds__(kSortThreads) bin_count_kernel(const TC* __restrict__ x, int soa, long long N,
+                                                                 SortGeom sg, unsigned int* __restrict__ counts,
+                                                                 int* range_flag) {
+  extern __shared__ unsigned int hist[];
+  const bool sm = sg.ntiles <= kSmemBins;
+  if (sm) {
+    for (int i = threadIdx.x; i < sg.ntiles; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+  }
+  bool bad = false;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    TR q[3];
+    const int t = tile_of<D, TC, TR>(x, soa, N, n, sg, q, bad);
+    if (sm) atomicAdd(&hist[t], 1u);
+    else atomicAdd(&counts[t], 1u);
+  }
+  if (bad) atomicOr(range_flag, 1);
+  if (sm) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < sg.ntiles; i += blockDim.x)
+      if (hist[i]) atomicAdd(&counts[i], hist[i]);
+  }
+}
+
+// exclusive scan of tile counts (one block; tile counts are small)
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(const unsigned int* __restrict__ counts, int ntiles,
+                                                          long long* __restrict__ tile_off,
+                                                          long long* __restrict__ cursor) {
+  __shared__ long long part[1024];
+  const int per = (ntiles + blockDim.x - 1) / blockDim.x;
+  const int a = threadIdx.x * per, b = min(ntiles, a + per);
+  long long s = 0;
+  for (int i = a; i < b; ++i) s += counts[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      const long long v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    tile_off[ntiles] = run;
+  }
+  __syncthreads();
+  long long run = part[threadIdx.x];
+  for (int i = a; i < b; ++i) {
+    tile_off[i] = run;
+    cursor[i] = run;
+    run += counts[i];
+  }
+}
+
+template <int D, typename TC, typename TV, typename TR>
+__global__ void __launch_bounds__(kSortThreads) bin_scatter_kernel(const TC* __restrict__ x, const TV* __restrict__ y,
+                                                                   int soa, long long N, SortGeom sg,
+                                                                   long long* __restrict__ cursor,
+                                                                   TR* __restrict__ rec) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const bool sm = sg.ntiles <= kSmemBins;
+  long long* base = reinterpret_cast<long long*>(smraw);
+  unsigned int* hist = reinterpret_cast<unsigned int*>(base + (sm ? sg.ntiles : 0));
+  const long long chunk = (long long)blockDim.x * kScatterPPT;
+  for (long long c0 = blockIdx.x * chunk; c0 < N; c0 += (long long)gridDim.x * chunk) {
+    int tt[kScatterPPT];
+    unsigned int rk[kScatterPPT];
+    TR qq[kScatterPPT][D];
+    TR yy[kScatterPPT];
+    if (sm) {
+      for (int i = threadIdx.x; i < sg.ntiles; i += blockDim.x) hist[i] = 0u;
+      __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < kScatterPPT; ++p) {
+      const long long n = c0 + (long long)p * blockDim.x + threadIdx.x;
+      tt[p] = -1;
+      if (n < N) {
+        bool bad = false;
+        TR q[3];
+        tt[p] = tile_of<D, TC, TR>(x, soa, N, n, sg, q, bad);
+#pragma unroll
+        for (int a = 0; a < D; ++a) qq[p][a] = q[a];
+        yy[p] = (TR)y[n];
+        if (sm) rk[p] = atomicAdd(&hist[tt[p]], 1u);
+      }
+      if (!sm) {
+        // warp-aggregated reservation directly in the global cursors
+        const unsigned int act = __ballot_sync(0xffffffffu, tt[p] >= 0);
+        if (tt[p] >= 0) {
+          const unsigned int peers = __match_any_sync(act, tt[p]);
+          const int leader = __ffs(peers) - 1;
+          const int lane = threadIdx.x & 31;
+          unsigned long long b0 = 0;
+          if (lane == leader) b0 = atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[tt[p]]),
+                                             (unsigned long long)__popc(peers));
+          b0 = __shfl_sync(peers, b0, leader);
+          const long long pos = (long long)b0 + __popc(peers & ((1u << lane) - 1u));
+#pragma unroll
+          for (int a = 0; a < D; ++a) rec[(long long)a * N + pos] = qq[p][a];
+          rec[(long long)D * N + pos] = yy[p];
+        }
+      }
+    }
+    if (sm) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < sg.ntiles; i += blockDim.x) {
+        const unsigned int h = hist[i];
+        if (h) base[i] = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[i]), (unsigned long long)h);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < kScatterPPT; ++p) {
+        if (tt[p] >= 0) {
+          const long long pos = base[tt[p]] + rk[p];
+#pragma unroll
+          for (int a = 0; a < D; ++a) rec[(long long)a * N + pos] = qq[p][a];
+          rec[(long long)D * N + pos] = yy[p];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------- spread
+// One block per segment of the sorted records; for every tile the segment
+// overlaps, accumulate that tile's points into a shared-memory tile (with
+// halo) in TR precision, then add the tile into the FP64 extended grid.
+template <int D, int W, typename TR>
+__global__ void __launch_bounds__(256) spread_kernel(const TR* __restrict__ rec, long long N, SortGeom sg,
+                                                     const long long* __restrict__ tile_off, long long seg_len,
+                                                     EsCoef<TR> cf, double2* __restrict__ E) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TR* acc = reinterpret_cast<TR*>(smraw);
+  __shared__ int t_first;
+  const int TB = sg.TB;
+  const int S = TB + W - 1;
+  int cells = S;
+  if (D > 1) cells *= S;
+  if (D > 2) cells *= S;
+  const long long s0 = blockIdx.x * seg_len;
+  const long long s1 = min(N, s0 + seg_len);
+  if (s0 >= s1) return;
+  if (threadIdx.x == 0) {
+    // largest t < ntiles with tile_off[t] <= s0
+    int lo = 0, hi = sg.ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= s0) lo = mid; else hi = mid - 1;
+    }
+    t_first = lo;
+  }
+  __syncthreads();
+  for (int t = t_first; t < sg.ntiles; ++t) {
+    const long long ta = tile_off[t], tb = tile_off[t + 1];
+    if (ta >= s1) break;
+    const long long a = max(s0, ta), b = min(s1, tb);
+    if (a >= b) continue;
+    for (int c = threadIdx.x; c < 2 * cells; c += blockDim.x) acc[c] = TR(0);
+    __syncthreads();
+    for (long long i = a + threadIdx.x; i < b; i += blockDim.x) {
+      TR wt[D][W];
+      int lb[D];
+#pragma unroll
+      for (int dd = 0; dd < D; ++dd) {
+        const TR qv = rec[(long long)dd * N + i];
+        int l = (int)floor(qv);
+        l = max(0, min(l, TB - 1));
+        lb[dd] = l;
+        es_weights<TR, W>(qv - (TR)l, cf, wt[dd]);
+      }
+      const TR yv = rec[(long long)D * N + i];
+      if (D == 1) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+          TR* c = acc + 2 * (lb[0] + u);
+          atomicAdd(c, wt[0][u]);
+          atomicAdd(c + 1, wt[0][u] * yv);
+        }
+      } else if (D == 2) {
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+          const TR wa = wt[0][u], wy = wa * yv;
+          TR* row = acc + 2 * ((lb[0] + u) * S + lb[1]);
+#pragma unroll
+          for (int v = 0; v < W; ++v) {
+            atomicAdd(row + 2 * v, wa * wt[D - 1][v]);
+            atomicAdd(row + 2 * v + 1, wy * wt[D - 1][v]);
+          }
+        }
+      } else {
+        for (int u = 0; u < W; ++u) {
+#pragma unroll
+          for (int v = 0; v < W; ++v) {
+            const TR wa = wt[0][u] * wt[1 % D][v], wy = wa * yv;
+            TR* row = acc + 2 * (((lb[0] + u) * S + lb[1 % D] + v) * S + lb[D - 1]);
+#pragma unroll
+            for (int z = 0; z < W; ++z) {
+              atomicAdd(row + 2 * z, wa * wt[D - 1][z]);
+              atomicAdd(row + 2 * z + 1, wy * wt[D - 1][z]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // flush the tile into the FP64 extended grid
+    int tcv[3];
+    {
+      int r = t;
+      for (int dd = D - 1; dd >= 0; --dd) {
+        tcv[dd] = r % sg.nt[dd];
+        r /= sg.nt[dd];
+      }
+    }
+    for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+      const TR re = acc[2 * c], im = acc[2 * c + 1];
+      if (re == TR(0) && im == TR(0)) continue;
+      int rem = c;
+      long long gi = 0;
+      bool inside = true;
+      int loc[3];
+      for (int dd = D - 1; dd >= 0; --dd) {
+        loc[dd] = rem % S;
+        rem /= S;
+      }
+      for (int dd = 0; dd < D; ++dd) {
+        const int e = tcv[dd] * TB + loc[dd];
+        inside = inside && (e < sg.nEx);
+        gi = gi * sg.nEx + e;
+      }
+      if (inside) {
+        atomicAdd(&E[gi].x, (double)re);
+        atomicAdd(&E[gi].y, (double)im);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Register-accumulating spread (FP32 records, d = 1 or 2, W <= 8).  The
+// points of a tile are processed in batches: a counting sort in shared
+// memory groups each batch by fine-grid cell, then thread t, which owns
+// cell t of the tile, adds the weights of every point of its cell into a
+// W^d footprint held in registers.  The registers are added into the
+// shared-memory tile in W^d phases in which all threads write distinct
+// cells (no atomics), and the tile is flushed to the FP64 extended grid
+// once per tile visit.
+constexpr int kRegThreads = 256;
+constexpr int kRegBatch = 8192;
+constexpr int kRegBatchPad = kRegBatch + kRegBatch / 32;
+
+template <int D> struct RegTile;
+template <> struct RegTile<1> { static constexpr int TB = 256; };
+template <> struct RegTile<2> { static constexpr int TB = 16; };
+
+__device__ __forceinline__ int pad32(int p) { return p + (p >> 5); }
+
+// exclusive block scan of one int per thread (blockDim.x == kRegThreads)
+__device__ __forceinline__ int block_excl_scan(int v, int* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < kRegThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kRegThreads / 32) warp_tot[lane] = w;   // inclusive warp prefix
+  }
+  __syncthreads();
+  const int before = wid > 0 ? warp_tot[wid - 1] : 0;
+  return before + x - v;
+}
+
+template <int D>
+__device__ __forceinline__ int reg_cell(const float* q, float* f) {
+  constexpr int TB = RegTile<D>::TB;
+  int c = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    int l = (int)floorf(q[a]);
+    l = max(0, min(l, TB - 1));
+    f[a] = q[a] - (float)l;
+    c = c * TB + l;
+  }
+  return c;
+}
+
+template <int D, int W>
+__global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float* __restrict__ rec, long long N,
+                                                                     SortGeom sg, const long long* __restrict__ tile_off,
+                                                                     long long seg_len, EsCoef<float> cf,
+                                                                     double2* __restrict__ E) {
+  constexpr int TB = RegTile<D>::TB;
+  constexpr int S = TB + W - 1;
+  constexpr int CELLS = (D == 1) ? S : S * S;
+  constexpr int FP = (D == 1) ? W : W * W;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* sf = reinterpret_cast<float*>(smraw);            // D x kRegBatchPad fractional offsets
+  float* sy = sf + D * kRegBatchPad;                        // kRegBatchPad values
+  float* tile = sy + kRegBatchPad;                          // 2*CELLS
+  int* cnt = reinterpret_cast<int*>(tile + 2 * CELLS);      // kRegThreads
+  int* cur = cnt + kRegThreads;                             // kRegThreads
+  int* wtot = cur + kRegThreads;                            // 32
+  __shared__ int t_first;
+  const int t = threadIdx.x;
+  const long long s0 = blockIdx.x * seg_len;
+  const long long s1 = min(N, s0 + seg_len);
+  if (s0 >= s1) return;
+  if (t == 0) {
+    int lo = 0, hi = sg.ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= s0) lo = mid; else hi = mid - 1;
+    }
+    t_first = lo;
+  }
+  __syncthreads();
+  // cell owned by this thread
+  int own[D];
+  {
+    int r = t;
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      own[a] = r % TB;
+      r /= TB;
+    }
+  }
+  for (int tt = t_first; tt < sg.ntiles; ++tt) {
+    const long long ta = tile_off[tt], tb = tile_off[tt + 1];
+    if (ta >= s1) break;
+    const long long a0 = max(s0, ta), b0 = min(s1, tb);
+    if (a0 >= b0) continue;
+    float are[FP], aim[FP];
+#pragma unroll
+    for (int i = 0; i < FP; ++i) are[i] = aim[i] = 0.f;
+    for (long long p0 = a0; p0 < b0; p0 += kRegBatch) {
+      const int nbat = (int)min((long long)kRegBatch, b0 - p0);
+      cnt[t] = 0;
+      __syncthreads();
+      for (int k = t; k < nbat; k += kRegThreads) {
+        float q[D], f[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) q[a] = rec[(long long)a * N + p0 + k];
+        atomicAdd(&cnt[reg_cell<D>(q, f)], 1);
+      }
+      __syncthreads();
+      const int mine = cnt[t];
+      const int st = block_excl_scan(mine, wtot);
+      cur[t] = st;
+      __syncthreads();
+      for (int k = t; k < nbat; k += kRegThreads) {
+        float q[D], f[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) q[a] = rec[(long long)a * N + p0 + k];
+        const float yv = rec[(long long)D * N + p0 + k];
+        const int pos = pad32(atomicAdd(&cur[reg_cell<D>(q, f)], 1));
+#pragma unroll
+        for (int a = 0; a < D; ++a) sf[a * kRegBatchPad + pos] = f[a];
+        sy[pos] = yv;
+      }
+      __syncthreads();
+      for (int k = 0; k < mine; ++k) {
+        const int pos = pad32(st + k);
+        float w0[W], w1[W];
+        es_weights<float, W>(sf[pos], cf, w0);
+        const float yv = sy[pos];
+        if (D == 1) {
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            are[u] += w0[u];
+            aim[u] = fmaf(w0[u], yv, aim[u]);
+          }
+        } else {
+          es_weights<float, W>(sf[(D - 1) * kRegBatchPad + pos], cf, w1);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const float wa = w0[u], wy = w0[u] * yv;
+#pragma unroll
+            for (int v = 0; v < W; ++v) {
+              are[u * W + v] = fmaf(wa, w1[v], are[u * W + v]);
+              aim[u * W + v] = fmaf(wy, w1[v], aim[u * W + v]);
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // registers -> shared tile, one footprint offset per phase
+    for (int c = t; c < 2 * CELLS; c += kRegThreads) tile[c] = 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < FP; ++i) {
+      int cell;
+      if (D == 1) cell = own[0] + i;
+      else cell = (own[0] + i / W) * S + own[D - 1] + i % W;
+      tile[2 * cell] += are[i];
+      tile[2 * cell + 1] += aim[i];
+      __syncthreads();
+    }
+    // shared tile -> FP64 extended grid
+    int tcv[3] = {0, 0, 0};
+    {
+      int r = tt;
+      for (int dd = D - 1; dd >= 0; --dd) {
+        tcv[dd] = r % sg.nt[dd];
+        r /= sg.nt[dd];
+      }
+    }
+    for (int c = t; c < CELLS; c += kRegThreads) {
+      const float re = tile[2 * c], im = tile[2 * c + 1];
+      if (re == 0.f && im == 0.f) continue;
+      int loc[2];
+      if (D == 1) loc[0] = c;
+      else { loc[0] = c / S; loc[1] = c % S; }
+      long long gi = 0;
+      bool inside = true;
+      for (int dd = 0; dd < D; ++dd) {
+        const int e = tcv[dd] * TB + loc[dd];
+        inside = inside && (e < sg.nEx);
+        gi = gi * sg.nEx + e;
+      }
+      if (inside) {
+        atomicAdd(&E[gi].x, (double)re);
+        atomicAdd(&E[gi].y, (double)im);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t spread_reg_smem(int d, int W) {
+  const int TB = d == 1 ? RegTile<1>::TB : RegTile<2>::TB;
+  const int S = TB + W - 1;
+  const int cells = d == 1 ? S : S * S;
+  return sizeof(float) * ((size_t)(d + 1) * kRegBatchPad + 2 * cells) + sizeof(int) * (2 * kRegThreads + 32);
+}
+
+// ---------------------------------------------------------------- fold / deconvolve
+// P[p] = sum of E[e] over extended indices e = (p + off) mod nf + j*nf < nEx
+template <int D, typename T>
+__global__ void fold_kernel(const double2* __restrict__ E, int nEx, int off, int nf, cplx<T>* __restrict__ P) {
+  long long total = nf;
+  if (D > 1) total *= nf;
+  if (D > 2) total *= nf;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int p[3] = {0, 0, 0};
+    long long r = idx;
+    for (int a = D - 1; a >= 0; --a) {
+      p[a] = (int)(r % nf);
+      r /= nf;
+    }
+    int e0[3];
+    for (int a = 0; a < D; ++a) e0[a] = (p[a] + off) % nf;
+    double sx = 0.0, sy = 0.0;
+    for (int i0 = e0[0]; i0 < nEx; i0 += nf) {
+      if (D == 1) {
+        const double2 v = E[i0];
+        sx += v.x;
+        sy += v.y;
+        continue;
+      }
+      for (int i1 = e0[1 % D]; i1 < nEx; i1 += nf) {
+        if (D == 2) {
+          const double2 v = E[(long long)i0 * nEx + i1];
+          sx += v.x;
+          sy += v.y;
+          continue;
+        }
+        for (int i2 = e0[D - 1]; i2 < nEx; i2 += nf) {
+          const double2 v = E[((long long)i0 * nEx + i1) * nEx + i2];
+          sx += v.x;
+          sy += v.y;
+        }
+      }
+    }
+    P[idx] = mk<T>((T)sx, (T)sy);
+  }
+}
+
+// Modes k in J_{2m}: G = FFT of the packed grid.  With G1 and Gy the
+// transforms of the real grids of strengths 1 and y:
+//   G1(k) = (G(k) + conj G(-k))/2,  Gy(k) = (G(k) - conj G(-k))/(2i).
+// w_k = G1(k)/prod psihat, b_j = D_j Gy(j)/prod psihat for j in J_m.
+template <int D, typename T>
+__global__ void deconv_split_kernel(const cplx<T>* __restrict__ G, int nf, int m, const double* __restrict__ corr,
+                                    const double* __restrict__ Dw, double2* __restrict__ w, double2* __restrict__ b) {
+  const int K = 4 * m + 1, n1 = 2 * m + 1;
+  long long total = K;
+  if (D > 1) total *= K;
+  if (D > 2) total *= K;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int k[3] = {0, 0, 0};
+    long long r = idx;
+    for (int a = D - 1; a >= 0; --a) {
+      k[a] = (int)(r % K) - 2 * m;
+      r /= K;
+    }
+    long long ip = 0, im = 0;
+    double c = 1.0;
+    bool inner = true;
+    long long jflat = 0;
+    for (int a = 0; a < D; ++a) {
+      const int kp = ((k[a] % nf) + nf) % nf;
+      const int km = ((-k[a] % nf) + nf) % nf;
+      ip = ip * nf + kp;
+      im = im * nf + km;
+      c *= corr[k[a] + 2 * m];
+      inner = inner && (k[a] >= -m && k[a] <= m);
+      jflat = jflat * n1 + (k[a] + m);
+    }
+    const cplx<T> gp = G[ip], gm = G[im];
+    const double gpx = gp.x, gpy = gp.y, gmx = gm.x, gmy = gm.y;
+    w[idx] = make_double2(0.5 * c * (gpx + gmx), 0.5 * c * (gpy - gmy));
+    if (inner) {
+      const double dc = Dw[jflat] * c;
+      b[jflat] = make_double2(0.5 * dc * (gpy + gmy), -0.5 * dc * (gpx - gmx));
+    }
+  }
+}
+
+// grid (L^d, complex FP64): w_k at k mod L for k in J_{2m}, zero elsewhere
+template <int D>
+__global__ void place_w_kernel(const double2* __restrict__ w, int m, int L, double2* __restrict__ grid) {
+  const int K = 4 * m + 1;
+  long long total = L;
+  if (D > 1) total *= L;
+  if (D > 2) total *= L;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx;
+    long long src = 0;
+    bool ok = true;
+    int g[3];
+    for (int a = D - 1; a >= 0; --a) {
+      g[a] = (int)(r % L);
+      r /= L;
+    }
+    for (int a = 0; a < D; ++a) {
+      int k;
+      if (g[a] <= 2 * m) k = g[a];
+      else if (g[a] >= L - 2 * m) k = g[a] - L;
+      else { ok = false; k = 0; }
+      src = src * K + (k + 2 * m);
+    }
+    grid[idx] = ok ? w[src] : make_double2(0.0, 0.0);
+  }
+}
+
+template <typename T>
+__global__ void extract_what_kernel(const double2* __restrict__ grid, long long n, double scale, T* __restrict__ what) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    what[i] = (T)(grid[i].x * scale);
+}
+
+// D_j = sqrt(h^d khat(h |j|)) on J_m (eq. 117), row-major, FP64.
+// SE: khat = c exp(-b xi^2); Matern: khat = c (a + b xi^2)^(-e).
+__global__ void spectral_weights_kernel(double* __restrict__ Dw, int m, int d, double h, int matern, double c,
+                                        double a, double b, double e) {
+  const int n1 = 2 * m + 1;
+  long long total = n1;
+  for (int i = 1; i < d; ++i) total *= n1;
+  const double hd = d == 1 ? h : (d == 2 ? h * h : h * h * h);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx;
+    double j2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double j = (double)(r % n1) - m;
+      r /= n1;
+      j2 += j * j;
+    }
+    const double xi2 = h * h * j2;
+    const double kh = matern ? c * pow(a + b * xi2, -e) : c * exp(-b * xi2);
+    Dw[idx] = sqrt(hd * kh);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+static int grid_for(long long n, int threads, int cap = 4096) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kern, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int D, typename TC, typename TR>
+static cudaError_t count_d(const void* x, int soa, long long N, const SortGeom& sg, unsigned int* counts, int* flag,
+                           cudaStream_t s) {
+  const size_t sm = sg.ntiles <= kSmemBins ? sg.ntiles * sizeof(unsigned int) : 0;
+  auto k = bin_count_kernel<D, TC, TR>;
+  cudaError_t e = allow_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = grid_for(N, kSortThreads, nsm * 8);
+  k<<<blocks, kSortThreads, sm, s>>>(reinterpret_cast<const TC*>(x), soa, N, sg, counts, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_count(const void* x, int coord_f64, int rec_f64, int soa, long long N, const SortGeom& sg,
+                             unsigned int* counts, int* range_flag, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  // the tile map uses the same arithmetic (record precision) as the scatter
+#define EFGP_CNT(DD)                                                                                        \
+  if (sg.d == DD) {                                                                                         \
+    if (coord_f64) return rec_f64 ? count_d<DD, double, double>(x, soa, N, sg, counts, range_flag, s)      \
+                                  : count_d<DD, double, float>(x, soa, N, sg, counts, range_flag, s);      \
+    return rec_f64 ? count_d<DD, float, double>(x, soa, N, sg, counts, range_flag, s)                      \
+                   : count_d<DD, float, float>(x, soa, N, sg, counts, range_flag, s);                      \
+  }
+  EFGP_CNT(1) EFGP_CNT(2) EFGP_CNT(3)
+#undef EFGP_CNT
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scan_tiles(const unsigned int* counts, int ntiles, long long* tile_off, long long* cursor,
+                              cudaStream_t s) {
+  scan_tiles_kernel<<<1, 1024, 0, s>>>(counts, ntiles, tile_off, cursor);
+  return cudaGetLastError();
+}
+
+template <int D, typename TC, typename TV, typename TR>
+static cudaError_t scatter_d(const void* x, const void* y, int soa, long long N, const SortGeom& sg, long long* cursor,
+                             void* rec, cudaStream_t s) {
+  const size_t sm = sg.ntiles <= kSmemBins ? sg.ntiles * (sizeof(long long) + sizeof(unsigned int)) : 0;
+  auto k = bin_scatter_kernel<D, TC, TV, TR>;
+  cudaError_t e = allow_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = grid_for(N, kSortThreads * kScatterPPT, nsm * 8);
+  k<<<blocks, kSortThreads, sm, s>>>(reinterpret_cast<const TC*>(x), reinterpret_cast<const TV*>(y), soa, N, sg, cursor,
+                                     reinterpret_cast<TR*>(rec));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_scatter(const void* x, int coord_f64, const void* y, int value_f64, int soa, long long N,
+                               const SortGeom& sg, int rec_f64, long long* cursor, void* rec, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  const SortGeom& g = sg;
+#define EFGP_SC(DD, TC, TV)                                                                  \
+  return rec_f64 ? scatter_d<DD, TC, TV, double>(x, y, soa, N, g, cursor, rec, s)           \
+                 : scatter_d<DD, TC, TV, float>(x, y, soa, N, g, cursor, rec, s);
+#define EFGP_SCD(DD)                                                \
+  if (sg.d == DD) {                                                 \
+    if (coord_f64 && value_f64) { EFGP_SC(DD, double, double) }     \
+    if (coord_f64 && !value_f64) { EFGP_SC(DD, double, float) }     \
+    if (!coord_f64 && value_f64) { EFGP_SC(DD, float, double) }     \
+    EFGP_SC(DD, float, float)                                       \
+  }
+  EFGP_SCD(1) EFGP_SCD(2) EFGP_SCD(3)
+#undef EFGP_SCD
+#undef EFGP_SC
+  return cudaErrorInvalidValue;
+}
+
+template <int D, int W, typename TR>
+static cudaError_t spread_dw(const void* rec, long long N, const SortGeom& sg, const long long* tile_off,
+                             const void* coef, double2* E, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  constexpr bool use_reg = std::is_same<TR, float>::value && (D == 1 || (D == 2 && W <= 7));
+  if constexpr (use_reg) {
+    if (sg.TB == RegTile<(D == 1 ? 1 : 2)>::TB) {
+      const size_t sm = spread_reg_smem(D, W);
+      auto k = spread_reg_kernel<(D == 1 ? 1 : 2), W>;
+      cudaError_t e = allow_smem(k, sm);
+      if (e != cudaSuccess) return e;
+      // equal-size segments, about four resident waves
+      long long nseg = (long long)nsm * 2 * 4;
+      long long seg = (N + nseg - 1) / nseg;
+      if (seg < 2048) seg = 2048;
+      nseg = (N + seg - 1) / seg;
+      k<<<(unsigned)nseg, kRegThreads, sm, s>>>(reinterpret_cast<const float*>(rec), N, sg, tile_off, seg,
+                                                *reinterpret_cast<const EsCoef<float>*>(coef), E);
+      return cudaGetLastError();
+    }
+  }
+  const int S = sg.TB + W - 1;
+  size_t cells = S;
+  if (D > 1) cells *= S;
+  if (D > 2) cells *= S;
+  const size_t sm = 2 * cells * sizeof(TR);
+  auto k = spread_kernel<D, W, TR>;
+  cudaError_t e = allow_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  // equal-size segments: enough blocks for several waves, each visiting
+  // few tiles
+  long long nseg = (long long)nsm * 8;
+  long long seg = (N + nseg - 1) / nseg;
+  if (seg < 1024) seg = 1024;
+  nseg = (N + seg - 1) / seg;
+  k<<<(unsigned)nseg, 256, sm, s>>>(reinterpret_cast<const TR*>(rec), N, sg, tile_off, seg,
+                                    *reinterpret_cast<const EsCoef<TR>*>(coef), E);
+  return cudaGetLastError();
+}
+
+template <int D, typename TR>
+static cudaError_t spread_d(const void* rec, long long N, const SortGeom& sg, const long long* tile_off,
+                            const void* coef, double2* E, cudaStream_t s) {
+  switch (sg.W) {
+    case 3: return spread_dw<D, 3, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 4: return spread_dw<D, 4, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 5: return spread_dw<D, 5, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 6: return spread_dw<D, 6, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 7: return spread_dw<D, 7, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 8: return spread_dw<D, 8, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 10: return spread_dw<D, 10, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 12: return spread_dw<D, 12, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 14: return spread_dw<D, 14, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 16: return spread_dw<D, 16, TR>(rec, N, sg, tile_off, coef, E, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_spread(const void* rec, int rec_f64, long long N, const SortGeom& sg, const long long* tile_off,
+                          const void* coef, double2* E, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  if (sg.d == 1) return rec_f64 ? spread_d<1, double>(rec, N, sg, tile_off, coef, E, s)
+                                : spread_d<1, float>(rec, N, sg, tile_off, coef, E, s);
+  if (sg.d == 2) return rec_f64 ? spread_d<2, double>(rec, N, sg, tile_off, coef, E, s)
+                                : spread_d<2, float>(rec, N, sg, tile_off, coef, E, s);
+  if (sg.d == 3) return rec_f64 ? spread_d<3, double>(rec, N, sg, tile_off, coef, E, s)
+                                : spread_d<3, float>(rec, N, sg, tile_off, coef, E, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_spectral_weights(double* Dw, int m, int d, double h, const efgp_kernel& k, cudaStream_t s) {
+  const double pi = 3.14159265358979323846;
+  const double var = k.variance > 0 ? k.variance : 1.0;
+  const double ell = k.lengthscale;
+  double c, a = 0.0, b, e = 0.0;
+  int matern = k.family == EFGP_KERNEL_MATERN;
+  if (!matern) {
+    c = var * std::pow(2.0 * pi * ell * ell, 0.5 * d);
+    b = 2.0 * pi * pi * ell * ell;
+  } else {
+    const double nu = k.nu;
+    c = var * std::pow(2.0, d) * std::pow(pi, 0.5 * d) * std::tgamma(nu + 0.5 * d) * std::pow(2.0 * nu, nu) /
+        (std::tgamma(nu) * std::pow(ell, 2.0 * nu));
+    a = 2.0 * nu / (ell * ell);
+    b = 4.0 * pi * pi;
+    e = nu + 0.5 * d;
+  }
+  long long total = 2 * m + 1;
+  for (int i = 1; i < d; ++i) total *= 2 * m + 1;
+  spectral_weights_kernel<<<grid_for(total, 256), 256, 0, s>>>(Dw, m, d, h, matern, c, a, b, e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold(const double2* E, int nEx, int off, int nf, int d, void* P, int p_f64, cudaStream_t s) {
+  long long total = nf;
+  for (int a = 1; a < d; ++a) total *= nf;
+  const int blocks = grid_for(total, 256);
+#define EFGP_FOLD(DD)                                                                                            \
+  if (d == DD) {                                                                                                 \
+    if (p_f64) fold_kernel<DD, double><<<blocks, 256, 0, s>>>(E, nEx, off, nf, reinterpret_cast<double2*>(P)); \
+    else fold_kernel<DD, float><<<blocks, 256, 0, s>>>(E, nEx, off, nf, reinterpret_cast<float2*>(P));         \
+    return cudaGetLastError();                                                                                   \
+  }
+  EFGP_FOLD(1) EFGP_FOLD(2) EFGP_FOLD(3)
+#undef EFGP_FOLD
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_deconv_split(const void* Phat, int p_f64, int nf, int d, int m, const double* corr1,
+                                const double* Dw, double2* w, double2* b, cudaStream_t s) {
+  long long total = 4 * m + 1;
+  for (int a = 1; a < d; ++a) total *= 4 * m + 1;
+  const int blocks = grid_for(total, 256);
+#define EFGP_DC(DD)                                                                                          \
+  if (d == DD) {                                                                                             \
+    if (p_f64)                                                                                               \
+      deconv_split_kernel<DD, double><<<blocks, 256, 0, s>>>(reinterpret_cast<const double2*>(Phat), nf, m, \
+                                                             corr1, Dw, w, b);                               \
+    else                                                                                                     \
+      deconv_split_kernel<DD, float><<<blocks, 256, 0, s>>>(reinterpret_cast<const float2*>(Phat), nf, m,   \
+                                                            corr1, Dw, w, b);                                \
+    return cudaGetLastError();                                                                               \
+  }
+  EFGP_DC(1) EFGP_DC(2) EFGP_DC(3)
+#undef EFGP_DC
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_place_w(const double2* w, int m, int d, int L, double2* grid, cudaStream_t s) {
+  long long total = L;
+  for (int a = 1; a < d; ++a) total *= L;
+  const int blocks = grid_for(total, 256);
+  if (d == 1) place_w_kernel<1><<<blocks, 256, 0, s>>>(w, m, L, grid);
+  else if (d == 2) place_w_kernel<2><<<blocks, 256, 0, s>>>(w, m, L, grid);
+  else place_w_kernel<3><<<blocks, 256, 0, s>>>(w, m, L, grid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract_what(const double2* grid, long long n, double scale, void* what, int what_f64,
+                                cudaStream_t s) {
+  const int blocks = grid_for(n, 256);
+  if (what_f64) extract_what_kernel<double><<<blocks, 256, 0, s>>>(grid, n, scale, reinterpret_cast<double*>(what));
+  else extract_what_kernel<float><<<blocks, 256, 0, s>>>(grid, n, scale, reinterpret_cast<float*>(what));
+  return cudaGetLastError();
+}
+
+}  // namespace efgp
