@@ -76,7 +76,7 @@ typedef struct {
   double cg_tol;        /* relative residual rho (0: eps/10; the Algorithm's step 4 uses  */
                         /* rho ~ eps, see efgp_solve)                                      */
   int64_t max_iter;     /* CG iteration cap (0: 100000)                                   */
-  double nufft_tol;     /* NUFFT accuracy (0: eps/10, Sec. 5.2)                           */
+  double nufft_tol;     /* NUFFT accuracy (0: eps/10, Sec. 5.1)                           */
   int m_override;       /* > 0: use this m instead of the Sec. 4.2 choice                 */
   double h_override;    /* > 0: use this h instead of the Sec. 4.2 choice                 */
   int fft_len_override; /* > 0: Toeplitz FFT length L per dim (>= 4m+1, 2,3,5,7-smooth)   */

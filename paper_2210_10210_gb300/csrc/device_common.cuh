@@ -43,11 +43,12 @@ template <typename C> __device__ __forceinline__ C cmul_si(C a, int s) {
 // piece j is a polynomial in t = 2f-1 with coefficients c[k*W + j].
 template <typename T, int W>
 __device__ __forceinline__ void es_weights(T f, const EsCoef<T>& cf, T (&wt)[W]) {
+  constexpr int DEG = es_degree(W);
   const T t = T(2) * f - T(1);
-  const int deg = cf.deg;
 #pragma unroll
-  for (int j = 0; j < W; ++j) wt[j] = cf.c[deg * W + j];
-  for (int k = deg - 1; k >= 0; --k) {
+  for (int j = 0; j < W; ++j) wt[j] = cf.c[DEG * W + j];
+#pragma unroll
+  for (int k = DEG - 1; k >= 0; --k) {
 #pragma unroll
     for (int j = 0; j < W; ++j) wt[j] = fma(wt[j], t, cf.c[k * W + j]);
   }

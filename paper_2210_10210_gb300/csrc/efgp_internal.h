@@ -22,6 +22,11 @@ constexpr int kMaxRadixPasses = 16;
 // ES widths with compiled spread/interp kernels; a requested width is rounded
 // up to the next one (a wider kernel is only more accurate).
 constexpr int kWidths[] = {3, 4, 5, 6, 7, 8, 10, 12, 14, 16};
+// Degree of the polynomial that replaces each piece of the ES kernel: fixed
+// per width so device code evaluates it fully unrolled with the coefficients
+// as constant operands (W+2 is at the accuracy plateau of the fit for the
+// upsampling factors used, set by the kernel's square-root edge).
+constexpr int es_degree(int w) { return w + 2; }
 
 void set_error(const std::string& msg);
 

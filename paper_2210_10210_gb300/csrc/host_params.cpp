@@ -320,21 +320,10 @@ int plan_nufft(int d, int K, double h, double tol, double cost_points, double up
       if (width_override > 0 && w < width_override) continue;
       if (w > nf / 2) continue;
       double beta = 0.97 * kPi * w * (1.0 - 1.0 / (2.0 * sig_eff));
-      // polynomial degree: raise until the fit is well below tol or stalls
-      std::vector<double> coef, cbest;
-      double ferr_prev = 1e300;
-      int deg = std::max(w - 1, 2), dbest = deg;
-      double fbest = 1e300;
-      for (int dg = deg; dg <= std::min(w + 6, kMaxDeg); ++dg) {
-        double fe = fit_pieces(w, beta, dg, coef);
-        if (fe < fbest) {
-          fbest = fe;
-          cbest = coef;
-          dbest = dg;
-        }
-        if (fe <= 0.05 * tol || fe > 0.5 * ferr_prev) break;
-        ferr_prev = fe;
-      }
+      // polynomial degree fixed per width (see es_degree)
+      std::vector<double> cbest;
+      const int dbest = es_degree(w);
+      fit_pieces(w, beta, dbest, cbest);
       std::vector<double> corr(2 * K + 1);
       for (int k = -K; k <= K; ++k) corr[k + K] = 1.0 / (0.5 * w * es_ft(kPi * w * k / (double)nf, beta, qx, qw));
       double err = point_error(nf, K, w, corr, cbest, dbest);

@@ -47,17 +47,28 @@ __global__ void __launch_bounds__(kSortThreads) bin_count_kernel(const TC* __res
                                                                  SortGeom sg, unsigned int* __restrict__ counts,
                                                                  int* range_flag) {
   extern __shared__ unsigned int hist[];
+  constexpr int U = 4;   // points per thread per step: keeps several loads in flight
   const bool sm = sg.ntiles <= kSmemBins;
   if (sm) {
     for (int i = threadIdx.x; i < sg.ntiles; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
   }
   bool bad = false;
-  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
-    TR q[3];
-    const int t = tile_of<D, TC, TR>(x, soa, N, n, sg, q, bad);
-    if (sm) atomicAdd(&hist[t], 1u);
-    else atomicAdd(&counts[t], 1u);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long n0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; n0 < N; n0 += U * stride) {
+    int t[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long n = n0 + u * stride;
+      TR q[3];
+      t[u] = n < N ? tile_of<D, TC, TR>(x, soa, N, n, sg, q, bad) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (t[u] < 0) continue;
+      if (sm) atomicAdd(&hist[t[u]], 1u);
+      else atomicAdd(&counts[t[u]], 1u);
+    }
   }
   if (bad) atomicOr(range_flag, 1);
   if (sm) {
@@ -164,6 +175,114 @@ __global__ void __launch_bounds__(kSortThreads) bin_scatter_kernel(const TC* __r
       }
       __syncthreads();
     }
+  }
+}
+
+
+// exclusive scan of one int per thread over a 256-thread block
+__device__ __forceinline__ int block_excl_scan256(int v, int* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < 8 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < 8) warp_tot[lane] = w;   // inclusive warp prefix
+  }
+  __syncthreads();
+  const int before = wid > 0 ? warp_tot[wid - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+// Sorting scatter: each block takes chunks of 256*PPT points, sorts a chunk
+// by tile in shared memory (counting sort), reserves one range per tile in
+// the global output with a single atomic per non-empty tile, and writes the
+// chunk out tile run by tile run, so that consecutive threads store
+// consecutive addresses.
+constexpr int kSortedScatterMaxTiles = 4096;
+
+template <int D, typename TC, typename TV, typename TR, int PPT>
+__global__ void __launch_bounds__(256) bin_scatter_sorted_kernel(const TC* __restrict__ x, const TV* __restrict__ y,
+                                                                 int soa, long long N, SortGeom sg,
+                                                                 long long* __restrict__ cursor,
+                                                                 TR* __restrict__ rec) {
+  constexpr int P = 256 * PPT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int T = sg.ntiles;
+  TR* sq = reinterpret_cast<TR*>(smraw);                                   // (D+1) x P
+  long long* base = reinterpret_cast<long long*>(sq + (size_t)(D + 1) * P);  // T
+  int* stile = reinterpret_cast<int*>(base + T);                           // P
+  unsigned int* hist = reinterpret_cast<unsigned int*>(stile + P);         // T
+  int* lstart = reinterpret_cast<int*>(hist + T);                          // T
+  __shared__ int wtot[8];
+  const int slice = (T + 255) / 256;
+  for (long long c0 = blockIdx.x * (long long)P; c0 < N; c0 += (long long)gridDim.x * P) {
+    for (int i = threadIdx.x; i < T; i += 256) hist[i] = 0u;
+    __syncthreads();
+    int tt[PPT];
+    unsigned int rk[PPT];
+    TR qq[PPT][D];
+    TR yy[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const long long n = c0 + (long long)p * 256 + threadIdx.x;
+      tt[p] = -1;
+      if (n < N) {
+        bool bad = false;
+        TR q[3];
+        tt[p] = tile_of<D, TC, TR>(x, soa, N, n, sg, q, bad);
+#pragma unroll
+        for (int a = 0; a < D; ++a) qq[p][a] = q[a];
+        yy[p] = (TR)y[n];
+        rk[p] = atomicAdd(&hist[tt[p]], 1u);
+      }
+    }
+    __syncthreads();
+    // exclusive scan of the chunk's tile histogram; reserve global ranges
+    {
+      const int a = threadIdx.x * slice, b = min(T, a + slice);
+      int sum = 0;
+      for (int i = a; i < b; ++i) sum += (int)hist[i];
+      int run = block_excl_scan256(sum, wtot);
+      for (int i = a; i < b; ++i) {
+        lstart[i] = run;
+        const unsigned int h = hist[i];
+        run += (int)h;
+        if (h) base[i] = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[i]),
+                                              (unsigned long long)h);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      if (tt[p] >= 0) {
+        const int pos = lstart[tt[p]] + (int)rk[p];
+#pragma unroll
+        for (int a = 0; a < D; ++a) sq[(size_t)a * P + pos] = qq[p][a];
+        sq[(size_t)D * P + pos] = yy[p];
+        stile[pos] = tt[p];
+      }
+    }
+    __syncthreads();
+    const int nvalid = (int)min((long long)P, N - c0);
+    for (int i = threadIdx.x; i < nvalid; i += 256) {
+      const int t = stile[i];
+      const long long g = base[t] + (i - lstart[t]);
+#pragma unroll
+      for (int a = 0; a <= D; ++a) rec[(long long)a * N + g] = sq[(size_t)a * P + i];
+    }
+    __syncthreads();
   }
 }
 
@@ -392,6 +511,7 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
       const int nbat = (int)min((long long)kRegBatch, b0 - p0);
       cnt[t] = 0;
       __syncthreads();
+#pragma unroll 4
       for (int k = t; k < nbat; k += kRegThreads) {
         float q[D], f[D];
 #pragma unroll
@@ -403,6 +523,7 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
       const int st = block_excl_scan(mine, wtot);
       cur[t] = st;
       __syncthreads();
+#pragma unroll 4
       for (int k = t; k < nbat; k += kRegThreads) {
         float q[D], f[D];
 #pragma unroll
@@ -686,13 +807,26 @@ cudaError_t launch_scan_tiles(const unsigned int* counts, int ntiles, long long*
 template <int D, typename TC, typename TV, typename TR>
 static cudaError_t scatter_d(const void* x, const void* y, int soa, long long N, const SortGeom& sg, long long* cursor,
                              void* rec, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (sg.ntiles <= kSortedScatterMaxTiles) {
+    constexpr int PPT = (sizeof(TR) == 8 || D == 3) ? 8 : 16;
+    constexpr int P = 256 * PPT;
+    const size_t sm = sizeof(TR) * (size_t)(D + 1) * P + sizeof(long long) * sg.ntiles + sizeof(int) * P +
+                      2 * sizeof(int) * sg.ntiles;
+    auto k = bin_scatter_sorted_kernel<D, TC, TV, TR, PPT>;
+    cudaError_t e = allow_smem(k, sm);
+    if (e != cudaSuccess) return e;
+    const int blocks = grid_for(N, P, nsm * 4);
+    k<<<blocks, 256, sm, s>>>(reinterpret_cast<const TC*>(x), reinterpret_cast<const TV*>(y), soa, N, sg, cursor,
+                              reinterpret_cast<TR*>(rec));
+    return cudaGetLastError();
+  }
   const size_t sm = sg.ntiles <= kSmemBins ? sg.ntiles * (sizeof(long long) + sizeof(unsigned int)) : 0;
   auto k = bin_scatter_kernel<D, TC, TV, TR>;
   cudaError_t e = allow_smem(k, sm);
   if (e != cudaSuccess) return e;
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = grid_for(N, kSortThreads * kScatterPPT, nsm * 8);
   k<<<blocks, kSortThreads, sm, s>>>(reinterpret_cast<const TC*>(x), reinterpret_cast<const TV*>(y), soa, N, sg, cursor,
                                      reinterpret_cast<TR*>(rec));
