@@ -70,6 +70,7 @@ SIGNATURES = [
                              C.c_double, C.POINTER(efgp_options), C.POINTER(C.c_void_p)]),
     ("efgp_solve", C.c_int, [C.c_void_p, C.POINTER(efgp_solve_info)]),
     ("efgp_predict", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    ("efgp_predict_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     ("efgp_destroy", None, [C.c_void_p]),
     ("efgp_get_params", C.c_int, [C.c_void_p, C.POINTER(efgp_params)]),
     ("efgp_get_beta", C.c_int, [C.c_void_p, C.c_void_p]),

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "handle.h"
 #include "kernels.h"
 
 using namespace efgp;
@@ -22,6 +23,11 @@ namespace efgp {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+bool fault_injected(const char* what) {
+  const char* e = std::getenv("EFGP_FAULT");
+  return e && std::strcmp(e, what) == 0;
+}
 
 }  // namespace efgp
 
@@ -51,16 +57,6 @@ long long ipow(long long b, int e) {
   return r;
 }
 
-// One pass of a multi-axis FFT or of the Toeplitz product.
-struct Pass {
-  LineGeom g;
-  int in_buf;   // buffer ids, interpreted by the caller
-  int out_buf;
-  int dir;
-  int inm, outm;
-  bool conv;
-  int threads;
-};
 
 int choose_nb(int L, long long inner, long long nlines, size_t elem) {
   int nb;
@@ -230,96 +226,9 @@ void pinned_put(char* p) {
 // max|y|, while eps/10 keeps them below 10 eps max|y|.
 double default_rho(double eps) { return eps / 10.0; }
 
-bool fault_injected(const char* what) {
-  const char* e = std::getenv("EFGP_FAULT");
-  return e && std::strcmp(e, what) == 0;
-}
 
 }  // namespace
 
-// ---------------------------------------------------------------------------
-struct efgp_handle {
-  int d = 0;
-  long long N = 0;
-  efgp_kernel kern{};
-  double sigma = 0, eps = 0;
-  efgp_options opt{};
-  efgp_params par{};
-  NufftPlan p1, p2;
-  int f64 = 0;          // FP64 grids/FFTs (plain precision)
-  size_t elem = 8;      // bytes of one complex grid element
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  long long M = 0;
-  int n1 = 0;
-  // device arrays
-  double* Dw = nullptr;
-  double* corr1 = nullptr;
-  double* corr2 = nullptr;
-  double2* w = nullptr;
-  double2* b = nullptr;
-  void* what = nullptr;
-  void* twL = nullptr;
-  void* twF2 = nullptr;
-  double2 *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
-  CgState* st = nullptr;
-  double* partials = nullptr;
-  void* scrA = nullptr;
-  void* scrB = nullptr;
-  void* g2 = nullptr;
-  void* E2 = nullptr;
-  int* flag = nullptr;
-  double* dsum = nullptr;
-  unsigned int* ticket = nullptr;
-  CgState* host_state = nullptr;
-  int* host_flag = nullptr;
-  char* pinned = nullptr;   // 256-byte pinned slot holding host_state and host_flag
-  // plans
-  std::vector<Pass> mv;
-  std::vector<Pass> fft2;
-  cudaGraphExec_t graph = nullptr;
-  int graph_iters = 0;
-  EsCoef<float> c1f{}, c2f{};
-  EsCoef<double> c1d{}, c2d{};
-  bool solved = false;
-  std::vector<void*> allocs;
-  efgp_phase_times times{};
-  cudaEvent_t ev[8] = {};
-  bool ev_made = false;
-
-  void mark(int i) {
-    if (!opt.profile) return;
-    if (!ev_made) {
-      for (auto& e : ev) cudaEventCreate(&e);
-      ev_made = true;
-    }
-    cudaEventRecord(ev[i], stream);
-  }
-  double span(int a, int b) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev[a], ev[b]) != cudaSuccess) return 0.0;
-    return ms;
-  }
-
-  int alloc(void** ptr, size_t bytes) {
-    if (fault_injected("alloc")) {
-      set_error("injected allocation failure (EFGP_FAULT=alloc)");
-      return EFGP_ENOMEM;
-    }
-    if (bytes == 0) bytes = 16;
-    // stream-ordered allocation from the device pool: cheap to repeat for
-    // every set-up, and released without a device-wide synchronisation
-    cudaError_t e = cudaMallocAsync(ptr, bytes, stream);
-    if (e != cudaSuccess) {
-      set_error(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
-      cudaGetLastError();
-      return e == cudaErrorMemoryAllocation ? EFGP_ENOMEM : EFGP_ECUDA;
-    }
-    allocs.push_back(*ptr);
-    return EFGP_OK;
-  }
-};
 
 // ---------------------------------------------------------------------------
 namespace {
@@ -834,6 +743,13 @@ int handle_create(int d, long long N, const efgp_kernel* kern, double sigma, dou
 }
 
 }  // namespace
+
+namespace efgp {
+int internal_grid_fft(efgp_handle* H, int n, int dir, void* grid, bool f64, const void* tw) {
+  return grid_fft(H, n, dir, grid, f64, tw);
+}
+GridScale internal_make_scale(const NufftPlan& p) { return make_scale(p); }
+}  // namespace efgp
 
 // ===========================================================================
 extern "C" {
