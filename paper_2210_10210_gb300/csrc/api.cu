@@ -48,8 +48,7 @@ namespace {
     if (s_ != EFGP_OK) return s_;    \
   } while (0)
 
-// spread tile edge per dimension (the register spread kernel needs 256 / 16)
-constexpr int kTileEdge[4] = {0, 256, 16, 8};
+constexpr int kTileEdge[4] = {0, tile_edge(1), tile_edge(2), tile_edge(3)};
 
 long long ipow(long long b, int e) {
   long long r = 1;
@@ -483,6 +482,10 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   const int value_f64 = H->opt.value_dtype == EFGP_F64;
   const int soa = H->opt.x_layout == 1;
   const size_t recb = f64 ? 8 : 4;
+  sg.x_vec = (reinterpret_cast<uintptr_t>(dx) % 8) == 0;
+  // record arrays padded to 16-byte multiples with slack after the end, so
+  // that aligned bulk-copy windows never leave the allocation
+  sg.rstride = ((N + 3) / 4) * 4 + 4;
 
   void *counts = nullptr, *toff = nullptr, *cursor = nullptr, *rec = nullptr, *E = nullptr, *P = nullptr;
   EFGP_CK(cudaMallocAsync(&counts, sizeof(unsigned int) * sg.ntiles, H->stream));
@@ -495,10 +498,10 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   temps.push_back(E);
   EFGP_CK(cudaMemsetAsync(counts, 0, sizeof(unsigned int) * sg.ntiles, H->stream));
   EFGP_CK(cudaMemsetAsync(E, 0, sizeof(double2) * nE_tot, H->stream));
-  EFGP_CK(cudaMemsetAsync(H->flag, 0, sizeof(int), H->stream));
+  EFGP_CK(cudaMemsetAsync(H->flag, 0, 4 * sizeof(int), H->stream));
 
   if (N > 0) {
-    EFGP_CK(cudaMallocAsync(&rec, recb * (size_t)N * (d + 1), H->stream));
+    EFGP_CK(cudaMallocAsync(&rec, recb * (size_t)sg.rstride * (d + 1), H->stream));
     temps.push_back(rec);
     H->mark(0);
     EFGP_CK(launch_bin_count(dx, coord_f64, (int)f64, soa, N, sg, (unsigned int*)counts, H->flag, H->stream));
@@ -512,10 +515,10 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
     H->mark(2);
     EFGP_CK(launch_scan_tiles((unsigned int*)counts, sg.ntiles, (long long*)toff, (long long*)cursor, H->stream));
     EFGP_CK(launch_bin_scatter(dx, coord_f64, dy, value_f64, soa, N, sg, (int)f64, (long long*)cursor, rec,
-                               H->stream));
+                               H->flag + 1, H->stream));
     H->mark(3);
     const void* coef = f64 ? (const void*)&H->c1d : (const void*)&H->c1f;
-    EFGP_CK(launch_spread(rec, (int)f64, N, sg, (const long long*)toff, coef, (double2*)E, H->stream));
+    EFGP_CK(launch_spread(rec, (int)f64, N, sg, (const long long*)toff, coef, (double2*)E, H->flag + 1, H->stream));
     H->times.launches += 4;
   }
   H->mark(4);
@@ -575,6 +578,13 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   EFGP_CK(launch_extract_what((const double2*)Lg, L_tot, 1.0 / (double)L_tot, H->what, (int)f64, H->stream));
   H->times.launches += 2;
   H->mark(6);
+  // bounded device waits (bulk-copy barriers) report through flag[1]
+  EFGP_CK(cudaMemcpyAsync(H->host_flag + 1, H->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
+  EFGP_CK(cudaStreamSynchronize(H->stream));
+  if (H->host_flag[1]) {
+    set_error("a bounded device-side wait for a bulk copy ran out");
+    return EFGP_ETIMEOUT;
+  }
   if (H->opt.profile) {
     EFGP_CK(cudaStreamSynchronize(H->stream));
     if (N > 0) {

@@ -27,6 +27,9 @@ constexpr int kWidths[] = {3, 4, 5, 6, 7, 8, 10, 12, 14, 16};
 // as constant operands (W+2 is at the accuracy plateau of the fit for the
 // upsampling factors used, set by the kernel's square-root edge).
 constexpr int es_degree(int w) { return w + 2; }
+// Edge (fine-grid cells) of the spread tiles by which points are binned; the
+// register spread kernel gives one thread per cell of a 256-cell tile.
+constexpr int tile_edge(int d) { return d == 1 ? 256 : (d == 2 ? 16 : 8); }
 
 void set_error(const std::string& msg);
 

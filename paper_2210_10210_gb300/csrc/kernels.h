@@ -57,6 +57,8 @@ struct SortGeom {
   int nt[3];        // tiles per dim
   int ntiles;
   int nEx;          // extended grid per dim (nt*TB + W - 1)
+  int x_vec;        // 1: row-major 2D float coordinates are 8-byte aligned (vector loads)
+  long long rstride;  // elements between the sorted record arrays (>= N + 4, multiple of 4)
 };
 
 cudaError_t launch_bin_count(const void* x, int coord_f64, int rec_f64, int soa, long long N, const SortGeom& sg,
@@ -64,9 +66,9 @@ cudaError_t launch_bin_count(const void* x, int coord_f64, int rec_f64, int soa,
 cudaError_t launch_scan_tiles(const unsigned int* counts, int ntiles, long long* tile_off, long long* cursor,
                               cudaStream_t s);
 cudaError_t launch_bin_scatter(const void* x, int coord_f64, const void* y, int value_f64, int soa, long long N,
-                               const SortGeom& sg, int rec_f64, long long* cursor, void* rec, cudaStream_t s);
+                               const SortGeom& sg, int rec_f64, long long* cursor, void* rec, int* err, cudaStream_t s);
 cudaError_t launch_spread(const void* rec, int rec_f64, long long N, const SortGeom& sg, const long long* tile_off,
-                          const void* coef, double2* E, cudaStream_t s);
+                          const void* coef, double2* E, int* err, cudaStream_t s);
 cudaError_t launch_spectral_weights(double* Dw, int m, int d, double h, const efgp_kernel& k, cudaStream_t s);
 cudaError_t launch_fold(const double2* E, int nEx, int off, int nf, int d, void* P, int p_f64, cudaStream_t s);
 cudaError_t launch_deconv_split(const void* Phat, int p_f64, int nf, int d, int m, const double* corr1,

@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace efgp {
 
@@ -17,13 +18,15 @@ constexpr int kScatterPPT = 8;        // points per thread per scatter chunk
 constexpr int kSmemBins = 8192;       // tiles handled with shared-memory histograms
 
 // ---------------------------------------------------------------- tile map
+// Tile of a point from its coordinates xa[0..D-1]; q receives the
+// tile-local footprint start plus sub-cell offset per axis.
 template <int D, typename TC, typename TR>
-__device__ __forceinline__ int tile_of(const TC* __restrict__ x, int soa, long long N, long long n, const SortGeom& sg,
-                                       TR (&q)[3], bool& bad) {
+__device__ __forceinline__ int tile_of_coords(const TC* xa_in, const SortGeom& sg, TR (&q)[3], bool& bad) {
+  constexpr int TB = tile_edge(D);
   int tc[3] = {0, 0, 0};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    TC xa = soa ? x[(long long)a * N + n] : x[n * D + a];
+    TC xa = xa_in[a];
     if (!(xa >= TC(0) && xa <= TC(1))) {  // also catches NaN
       bad = true;
       xa = TC(0);
@@ -32,14 +35,29 @@ __device__ __forceinline__ int tile_of(const TC* __restrict__ x, int soa, long l
     TR f;
     GridPos<TC, TR>::get(xa, sg.gs, l0, f);
     int e0 = l0 + sg.off;
-    e0 = max(0, min(e0, sg.nt[a] * sg.TB - 1));
-    tc[a] = e0 / sg.TB;
-    q[a] = (TR)(e0 - tc[a] * sg.TB) + f;   // tile-local footprint start + offset
+    e0 = max(0, min(e0, sg.nt[a] * TB - 1));
+    tc[a] = e0 / TB;
+    q[a] = (TR)(e0 - tc[a] * TB) + f;   // tile-local footprint start + offset
   }
   int t = tc[0];
   if (D > 1) t = t * sg.nt[1] + tc[1];
   if (D > 2) t = t * sg.nt[2] + tc[2];
   return t;
+}
+
+template <int D, typename TC, typename TR>
+__device__ __forceinline__ int tile_of(const TC* __restrict__ x, int soa, long long N, long long n, const SortGeom& sg,
+                                       TR (&q)[3], bool& bad) {
+  TC xa[3];
+  if (!soa && D == 2 && sizeof(TC) == 4 && sg.x_vec) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(x) + n);
+    xa[0] = (TC)v.x;
+    xa[1] = (TC)v.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) xa[a] = soa ? x[(long long)a * N + n] : x[n * D + a];
+  }
+  return tile_of_coords<D, TC, TR>(xa, sg, q, bad);
 }
 
 template <int D, typename TC, typename TR>
@@ -152,8 +170,8 @@ __global__ void __launch_bounds__(kSortThreads) bin_scatter_kernel(const TC* __r
           b0 = __shfl_sync(peers, b0, leader);
           const long long pos = (long long)b0 + __popc(peers & ((1u << lane) - 1u));
 #pragma unroll
-          for (int a = 0; a < D; ++a) rec[(long long)a * N + pos] = qq[p][a];
-          rec[(long long)D * N + pos] = yy[p];
+          for (int a = 0; a < D; ++a) rec[(long long)a * sg.rstride + pos] = qq[p][a];
+          rec[(long long)D * sg.rstride + pos] = yy[p];
         }
       }
     }
@@ -169,8 +187,8 @@ __global__ void __launch_bounds__(kSortThreads) bin_scatter_kernel(const TC* __r
         if (tt[p] >= 0) {
           const long long pos = base[tt[p]] + rk[p];
 #pragma unroll
-          for (int a = 0; a < D; ++a) rec[(long long)a * N + pos] = qq[p][a];
-          rec[(long long)D * N + pos] = yy[p];
+          for (int a = 0; a < D; ++a) rec[(long long)a * sg.rstride + pos] = qq[p][a];
+          rec[(long long)D * sg.rstride + pos] = yy[p];
         }
       }
       __syncthreads();
@@ -214,7 +232,7 @@ constexpr int kSortedScatterMaxTiles = 4096;
 
 template <int D, typename TC, typename TV, typename TR, int PPT>
 __global__ void __launch_bounds__(256) bin_scatter_sorted_kernel(const TC* __restrict__ x, const TV* __restrict__ y,
-                                                                 int soa, long long N, SortGeom sg,
+                                                                 int soa, long long N, long long n_begin, SortGeom sg,
                                                                  long long* __restrict__ cursor,
                                                                  TR* __restrict__ rec) {
   constexpr int P = 256 * PPT;
@@ -227,7 +245,7 @@ __global__ void __launch_bounds__(256) bin_scatter_sorted_kernel(const TC* __res
   int* lstart = reinterpret_cast<int*>(hist + T);                          // T
   __shared__ int wtot[8];
   const int slice = (T + 255) / 256;
-  for (long long c0 = blockIdx.x * (long long)P; c0 < N; c0 += (long long)gridDim.x * P) {
+  for (long long c0 = n_begin + blockIdx.x * (long long)P; c0 < N; c0 += (long long)gridDim.x * P) {
     for (int i = threadIdx.x; i < T; i += 256) hist[i] = 0u;
     __syncthreads();
     int tt[PPT];
@@ -280,10 +298,160 @@ __global__ void __launch_bounds__(256) bin_scatter_sorted_kernel(const TC* __res
       const int t = stile[i];
       const long long g = base[t] + (i - lstart[t]);
 #pragma unroll
-      for (int a = 0; a <= D; ++a) rec[(long long)a * N + g] = sq[(size_t)a * P + i];
+      for (int a = 0; a <= D; ++a) rec[(long long)a * sg.rstride + g] = sq[(size_t)a * P + i];
     }
     __syncthreads();
   }
+}
+
+
+// exclusive scan of one int per thread over an NT-thread block
+template <int NT>
+__device__ __forceinline__ int block_excl_scan_n(int v, int* warp_tot) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < NW ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NW) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  const int before = wid > 0 ? warp_tot[wid - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+// Sorting scatter fed by bulk asynchronous copies (FP32 row-major
+// coordinates and values): full chunks of 4096 points are copied into a
+// double-buffered shared staging area while the previous chunk is binned,
+// counting-sorted by tile and written out tile run by tile run.  The last
+// partial chunk is left to bin_scatter_sorted_kernel.
+constexpr int kTmaScatterThreads = 512;
+constexpr int kTmaScatterPPT = 8;
+constexpr int kTmaScatterChunk = kTmaScatterThreads * kTmaScatterPPT;
+
+template <int D>
+__global__ void __launch_bounds__(kTmaScatterThreads, 1)
+    bin_scatter_tma_kernel(const float* __restrict__ x, const float* __restrict__ y, long long nfull, long long N,
+                           SortGeom sg, long long* __restrict__ cursor, float* __restrict__ rec, int* err) {
+  constexpr int NT = kTmaScatterThreads, PPT = kTmaScatterPPT, P = kTmaScatterChunk;
+  constexpr int SB = (D + 1) * P;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int T = sg.ntiles;
+  float* stage = reinterpret_cast<float*>(smraw);
+  float* sq = stage + 2 * SB;
+  int* stile = reinterpret_cast<int*>(sq + SB);
+  long long* base = reinterpret_cast<long long*>(stile + P);
+  unsigned int* hist = reinterpret_cast<unsigned int*>(base + T);
+  int* lstart = reinterpret_cast<int*>(hist + T);
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int wtot[NT / 32];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  const uint32_t bytes_x = D * P * 4, bytes_y = P * 4;
+  long long c = blockIdx.x;
+  if (tid == 0 && c < nfull) {
+    mbar_arrive_expect_tx(&bar[0], bytes_x + bytes_y);
+    bulk_g2s(stage, x + c * (long long)P * D, bytes_x, &bar[0]);
+    bulk_g2s(stage + D * P, y + c * (long long)P, bytes_y, &bar[0]);
+  }
+  const int slice = (T + NT - 1) / NT;
+  int it = 0;
+  bool pending_other = false;
+  for (; c < nfull; c += gridDim.x, ++it) {
+    const int b = it & 1;
+    const long long cn = c + gridDim.x;
+    pending_other = cn < nfull;
+    if (tid == 0 && pending_other) {
+      float* dst = stage + (b ^ 1) * SB;
+      mbar_arrive_expect_tx(&bar[b ^ 1], bytes_x + bytes_y);
+      bulk_g2s(dst, x + cn * (long long)P * D, bytes_x, &bar[b ^ 1]);
+      bulk_g2s(dst + D * P, y + cn * (long long)P, bytes_y, &bar[b ^ 1]);
+    }
+    if (!mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), err)) abort_flag = 1;
+    for (int i = tid; i < T; i += NT) hist[i] = 0u;
+    __syncthreads();
+    if (abort_flag) break;
+    const float* sx = stage + b * SB;
+    int tt[PPT];
+    unsigned int rk[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const int k = p * NT + tid;
+      float xa[3];
+#pragma unroll
+      for (int a = 0; a < D; ++a) xa[a] = sx[k * D + a];
+      bool bad = false;
+      float q[3];
+      tt[p] = tile_of_coords<D, float, float>(xa, sg, q, bad);
+      rk[p] = atomicAdd(&hist[tt[p]], 1u);
+    }
+    __syncthreads();
+    {
+      const int a0 = tid * slice, a1 = min(T, a0 + slice);
+      int sum = 0;
+      for (int i = a0; i < a1; ++i) sum += (int)hist[i];
+      int run = block_excl_scan_n<NT>(sum, wtot);
+      for (int i = a0; i < a1; ++i) {
+        lstart[i] = run;
+        const unsigned int h = hist[i];
+        run += (int)h;
+        if (h) base[i] = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[i]),
+                                              (unsigned long long)h);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const int k = p * NT + tid;
+      float xa[3];
+#pragma unroll
+      for (int a = 0; a < D; ++a) xa[a] = sx[k * D + a];
+      bool bad = false;
+      float q[3];
+      tile_of_coords<D, float, float>(xa, sg, q, bad);
+      const int pos = lstart[tt[p]] + (int)rk[p];
+#pragma unroll
+      for (int a = 0; a < D; ++a) sq[a * P + pos] = q[a];
+      sq[D * P + pos] = sx[D * P + k];
+      stile[pos] = tt[p];
+    }
+    __syncthreads();
+    for (int i = tid; i < P; i += NT) {
+      const int t = stile[i];
+      const long long g = base[t] + (i - lstart[t]);
+#pragma unroll
+      for (int a = 0; a <= D; ++a) rec[(long long)a * sg.rstride + g] = sq[a * P + i];
+    }
+    __syncthreads();
+  }
+  // after an abandoned wait, let the copy already issued into the other
+  // buffer land (bounded) before the block's shared memory is released
+  if (abort_flag && tid == 0 && pending_other) mbar_wait_bounded(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1), err);
+}
+
+size_t scatter_tma_smem(int d, int ntiles) {
+  const size_t P = kTmaScatterChunk;
+  return sizeof(float) * (3 * (size_t)(d + 1) * P) + sizeof(int) * P + (sizeof(long long) + 2 * sizeof(int)) * ntiles;
 }
 
 // ---------------------------------------------------------------- spread
@@ -327,13 +495,13 @@ __global__ void __launch_bounds__(256) spread_kernel(const TR* __restrict__ rec,
       int lb[D];
 #pragma unroll
       for (int dd = 0; dd < D; ++dd) {
-        const TR qv = rec[(long long)dd * N + i];
+        const TR qv = rec[(long long)dd * sg.rstride + i];
         int l = (int)floor(qv);
         l = max(0, min(l, TB - 1));
         lb[dd] = l;
         es_weights<TR, W>(qv - (TR)l, cf, wt[dd]);
       }
-      const TR yv = rec[(long long)D * N + i];
+      const TR yv = rec[(long long)D * sg.rstride + i];
       if (D == 1) {
 #pragma unroll
         for (int u = 0; u < W; ++u) {
@@ -515,7 +683,7 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
       for (int k = t; k < nbat; k += kRegThreads) {
         float q[D], f[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) q[a] = rec[(long long)a * N + p0 + k];
+        for (int a = 0; a < D; ++a) q[a] = rec[(long long)a * sg.rstride + p0 + k];
         atomicAdd(&cnt[reg_cell<D>(q, f)], 1);
       }
       __syncthreads();
@@ -527,8 +695,8 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
       for (int k = t; k < nbat; k += kRegThreads) {
         float q[D], f[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) q[a] = rec[(long long)a * N + p0 + k];
-        const float yv = rec[(long long)D * N + p0 + k];
+        for (int a = 0; a < D; ++a) q[a] = rec[(long long)a * sg.rstride + p0 + k];
+        const float yv = rec[(long long)D * sg.rstride + p0 + k];
         const int pos = pad32(atomicAdd(&cur[reg_cell<D>(q, f)], 1));
 #pragma unroll
         for (int a = 0; a < D; ++a) sf[a * kRegBatchPad + pos] = f[a];
@@ -602,6 +770,296 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
     }
     __syncthreads();
   }
+}
+
+
+// Register-accumulating spread fed by bulk asynchronous copies (FP32
+// records, d = 1 or 2).  The sorted records of a block's segment are walked
+// as a sequence of batches (tile, first point, count); each batch's
+// coordinate and value runs are copied into one of two shared staging
+// buffers while the previous batch is processed.  A batch is counting-sorted
+// by fine cell through a 16-bit index array; two threads own each of the 256
+// cells of a tile and split the cell's points, each adding W^d weights into
+// registers.  The registers of a tile visit are added into a shared tile in
+// conflict-free phases and the tile is flushed to the FP64 grid.  The record
+// arrays are padded so that 16-byte aligned copy windows stay in bounds.
+constexpr int kTmaSpreadThreads = 512;
+constexpr int kTmaSpreadBatch = 8192;
+constexpr int kTmaSpreadSlot = kTmaSpreadBatch + 8;   // floats per staged array
+
+template <int D, int W>
+__global__ void __launch_bounds__(kTmaSpreadThreads, 1)
+    spread_tma_kernel(const float* __restrict__ rec, long long N, long long rstride, SortGeom sg,
+                      const long long* __restrict__ tile_off, long long seg_len, EsCoef<float> cf,
+                      double2* __restrict__ E, int* err) {
+  constexpr int TB = RegTile<D>::TB;
+  constexpr int S = TB + W - 1;
+  constexpr int CELLS = (D == 1) ? S : S * S;
+  constexpr int FP = (D == 1) ? W : W * W;
+  constexpr int NT = kTmaSpreadThreads;
+  constexpr int B = kTmaSpreadBatch;
+  constexpr int SLOT = kTmaSpreadSlot;
+  constexpr int NA = D + 1;   // staged arrays per batch
+  extern __shared__ __align__(128) unsigned char smraw[];
+  float* stage = reinterpret_cast<float*>(smraw);                 // 2 * NA * SLOT
+  float* tile = stage + 2 * NA * SLOT;                             // 2 * CELLS
+  unsigned short* idx = reinterpret_cast<unsigned short*>(tile + 2 * CELLS);  // B
+  int* cnt = reinterpret_cast<int*>(idx + B);                      // 256
+  int* cur = cnt + 256;                                            // 256
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int wtot[8];
+  __shared__ int it_tile[2], it_off[2];
+  __shared__ long long it_p0[2];
+  __shared__ int it_n[2];
+  __shared__ int abort_flag;
+  const int t = threadIdx.x;
+  const int cell = t & 255, half = t >> 8;
+  const long long s0 = blockIdx.x * seg_len;
+  const long long s1 = min(N, s0 + seg_len);
+  if (s0 >= s1) return;
+
+  // next batch after (tile tt, start p0): returns false at the segment end
+  auto next_item = [&](int& tt, long long& p0, int& n) -> bool {
+    long long b = min(s1, tile_off[tt + 1]);
+    p0 += n;
+    if (p0 < b) {
+      n = (int)min((long long)B, b - p0);
+      return true;
+    }
+    for (++tt; tt < sg.ntiles; ++tt) {
+      const long long ta = tile_off[tt];
+      if (ta >= s1) return false;
+      const long long a = max(s0, ta), bb = min(s1, tile_off[tt + 1]);
+      if (a < bb) {
+        p0 = a;
+        n = (int)min((long long)B, bb - a);
+        return true;
+      }
+    }
+    return false;
+  };
+  // copy the batch's arrays into staging buffer `slot`
+  auto issue = [&](int slot, long long p0, int n) {
+    const long long pa = p0 & ~3ll;
+    const long long pe = (p0 + n + 3) & ~3ll;
+    const uint32_t bytes = (uint32_t)((pe - pa) * 4);
+    mbar_arrive_expect_tx(&bar[slot], bytes * NA);
+    for (int a = 0; a < NA; ++a)
+      bulk_g2s(stage + (slot * NA + a) * SLOT, rec + a * rstride + pa, bytes, &bar[slot]);
+    it_off[slot] = (int)(p0 - pa);
+  };
+
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_barrier_init();
+    abort_flag = 0;
+    int lo = 0, hi = sg.ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= s0) lo = mid; else hi = mid - 1;
+    }
+    // first batch: the tile holding s0 (tiles before it may be empty)
+    int tt = lo;
+    long long p0 = s0;
+    int n = 0;
+    bool ok;
+    {
+      const long long b = min(s1, tile_off[tt + 1]);
+      if (p0 < b) {
+        n = (int)min((long long)B, b - p0);
+        ok = true;
+      } else {
+        n = 0;
+        ok = next_item(tt, p0, n);
+      }
+    }
+    it_tile[0] = ok ? tt : -1;
+    it_p0[0] = p0;
+    it_n[0] = n;
+    if (ok) issue(0, p0, n);
+  }
+  __syncthreads();
+
+  int own[D];
+  {
+    int r = cell;
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      own[a] = r % TB;
+      r /= TB;
+    }
+  }
+  float are[FP], aim[FP];
+#pragma unroll
+  for (int i = 0; i < FP; ++i) are[i] = aim[i] = 0.f;
+
+  int abort_it = -1;
+  for (int it = 0;; ++it) {
+    const int b = it & 1;
+    const int tt = it_tile[b];
+    if (tt < 0) break;
+    const long long p0 = it_p0[b];
+    const int n = it_n[b];
+    if (t == 0) {
+      int nt = tt;
+      long long np0 = p0;
+      int nn = n;
+      const bool ok = next_item(nt, np0, nn);
+      it_tile[b ^ 1] = ok ? nt : -1;
+      it_p0[b ^ 1] = np0;
+      it_n[b ^ 1] = nn;
+      if (ok) issue(b ^ 1, np0, nn);
+    }
+    if (!mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), err)) abort_flag = 1;
+    if (t < 256) cnt[t] = 0;
+    __syncthreads();
+    if (abort_flag) {
+      abort_it = it;
+      break;
+    }
+    const int off = it_off[b];
+    const float* sq0 = stage + (b * NA) * SLOT + off;
+    const float* sq1 = stage + (b * NA + (D - 1)) * SLOT + off;
+    const float* sy = stage + (b * NA + D) * SLOT + off;
+    // count by cell
+    for (int k = t; k < n; k += NT) {
+      float q[D], f[D];
+      q[0] = sq0[k];
+      if (D == 2) q[D - 1] = sq1[k];
+      atomicAdd(&cnt[reg_cell<D>(q, f)], 1);
+    }
+    __syncthreads();
+    int mine = 0, st = 0;
+    if (t < 256) {
+      mine = cnt[t];
+    }
+    // exclusive scan over the 256 cells by the first 256 threads
+    {
+      const int lane = t & 31, wid = t >> 5;
+      int x = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (wid < 8 && lane == 31) wtot[wid] = x;
+      __syncthreads();
+      if (wid == 0) {
+        int w = lane < 8 ? wtot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, w, o);
+          if (lane >= o) w += y;
+        }
+        if (lane < 8) wtot[lane] = w;
+      }
+      __syncthreads();
+      if (t < 256) {
+        st = (wid > 0 ? wtot[wid - 1] : 0) + x - mine;
+        cur[t] = st;
+      }
+    }
+    __syncthreads();
+    for (int k = t; k < n; k += NT) {
+      float q[D], f[D];
+      q[0] = sq0[k];
+      if (D == 2) q[D - 1] = sq1[k];
+      const int pos = atomicAdd(&cur[reg_cell<D>(q, f)], 1);
+      idx[pos] = (unsigned short)k;
+    }
+    __syncthreads();
+    // run of my cell: start = cur[cell] - cnt[cell] after the index pass
+    {
+      const int c_n = cnt[cell];
+      const int c_s = cur[cell] - c_n;
+      for (int j = half; j < c_n; j += 2) {
+        const int k = idx[c_s + j];
+        float w0[W], w1[W];
+        es_weights<float, W>(sq0[k] - (float)own[0], cf, w0);
+        const float yv = sy[k];
+        if (D == 1) {
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            are[u] += w0[u];
+            aim[u] = fmaf(w0[u], yv, aim[u]);
+          }
+        } else {
+          es_weights<float, W>(sq1[k] - (float)own[D - 1], cf, w1);
+#pragma unroll
+          for (int u = 0; u < W; ++u) {
+            const float wa = w0[u], wy = w0[u] * yv;
+#pragma unroll
+            for (int v = 0; v < W; ++v) {
+              are[u * W + v] = fmaf(wa, w1[v], are[u * W + v]);
+              aim[u * W + v] = fmaf(wy, w1[v], aim[u * W + v]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // last batch of this tile visit: registers -> shared tile -> FP64 grid
+    const int ntile = it_tile[b ^ 1];
+    if (ntile != tt) {
+      for (int c = t; c < 2 * CELLS; c += NT) tile[c] = 0.f;
+      __syncthreads();
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int i = 0; i < FP; ++i) {
+          if (half == h) {
+            int cc;
+            if (D == 1) cc = own[0] + i;
+            else cc = (own[0] + i / W) * S + own[D - 1] + i % W;
+            tile[2 * cc] += are[i];
+            tile[2 * cc + 1] += aim[i];
+          }
+          __syncthreads();
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < FP; ++i) are[i] = aim[i] = 0.f;
+      int tcv[2] = {0, 0};
+      {
+        int r = tt;
+        for (int dd = D - 1; dd >= 0; --dd) {
+          tcv[dd] = r % sg.nt[dd];
+          r /= sg.nt[dd];
+        }
+      }
+      for (int c = t; c < CELLS; c += NT) {
+        const float re = tile[2 * c], im = tile[2 * c + 1];
+        if (re == 0.f && im == 0.f) continue;
+        int loc[2];
+        if (D == 1) loc[0] = c;
+        else { loc[0] = c / S; loc[1] = c % S; }
+        long long gi = 0;
+        bool inside = true;
+        for (int dd = 0; dd < D; ++dd) {
+          const int e = tcv[dd] * TB + loc[dd];
+          inside = inside && (e < sg.nEx);
+          gi = gi * sg.nEx + e;
+        }
+        if (inside) {
+          atomicAdd(&E[gi].x, (double)re);
+          atomicAdd(&E[gi].y, (double)im);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // after an abandoned wait, let the copy already issued into the other
+  // buffer land (bounded) before the block's shared memory is released
+  if (abort_flag && t == 0 && abort_it >= 0 && it_tile[(abort_it & 1) ^ 1] >= 0)
+    mbar_wait_bounded(&bar[(abort_it & 1) ^ 1], (uint32_t)(((abort_it + 1) >> 1) & 1), nullptr);
+}
+
+size_t spread_tma_smem(int d, int W) {
+  const int TB = d == 1 ? RegTile<1>::TB : RegTile<2>::TB;
+  const int S = TB + W - 1;
+  const int cells = d == 1 ? S : S * S;
+  return sizeof(float) * (2 * (size_t)(d + 1) * kTmaSpreadSlot + 2 * cells) +
+         sizeof(unsigned short) * kTmaSpreadBatch + sizeof(int) * 512;
 }
 
 size_t spread_reg_smem(int d, int W) {
@@ -805,23 +1263,48 @@ cudaError_t launch_scan_tiles(const unsigned int* counts, int ntiles, long long*
 }
 
 template <int D, typename TC, typename TV, typename TR>
+static cudaError_t scatter_sorted(const void* x, const void* y, int soa, long long N, long long n_begin,
+                                  const SortGeom& sg, long long* cursor, void* rec, int nsm, cudaStream_t s) {
+  constexpr int PPT = (sizeof(TR) == 8 || D == 3) ? 8 : 16;
+  constexpr int P = 256 * PPT;
+  const size_t sm = sizeof(TR) * (size_t)(D + 1) * P + sizeof(long long) * sg.ntiles + sizeof(int) * P +
+                    2 * sizeof(int) * sg.ntiles;
+  auto k = bin_scatter_sorted_kernel<D, TC, TV, TR, PPT>;
+  cudaError_t e = allow_smem(k, sm);
+  if (e != cudaSuccess) return e;
+  const int blocks = grid_for(N - n_begin, P, nsm * 4);
+  k<<<blocks, 256, sm, s>>>(reinterpret_cast<const TC*>(x), reinterpret_cast<const TV*>(y), soa, N, n_begin, sg,
+                            cursor, reinterpret_cast<TR*>(rec));
+  return cudaGetLastError();
+}
+
+template <int D, typename TC, typename TV, typename TR>
 static cudaError_t scatter_d(const void* x, const void* y, int soa, long long N, const SortGeom& sg, long long* cursor,
-                             void* rec, cudaStream_t s) {
+                             void* rec, int* err, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (sg.ntiles <= kSortedScatterMaxTiles) {
-    constexpr int PPT = (sizeof(TR) == 8 || D == 3) ? 8 : 16;
-    constexpr int P = 256 * PPT;
-    const size_t sm = sizeof(TR) * (size_t)(D + 1) * P + sizeof(long long) * sg.ntiles + sizeof(int) * P +
-                      2 * sizeof(int) * sg.ntiles;
-    auto k = bin_scatter_sorted_kernel<D, TC, TV, TR, PPT>;
-    cudaError_t e = allow_smem(k, sm);
-    if (e != cudaSuccess) return e;
-    const int blocks = grid_for(N, P, nsm * 4);
-    k<<<blocks, 256, sm, s>>>(reinterpret_cast<const TC*>(x), reinterpret_cast<const TV*>(y), soa, N, sg, cursor,
-                              reinterpret_cast<TR*>(rec));
-    return cudaGetLastError();
+    if constexpr (std::is_same<TC, float>::value && std::is_same<TV, float>::value &&
+                  std::is_same<TR, float>::value) {
+      const size_t sm = scatter_tma_smem(D, sg.ntiles);
+      const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+      const long long nfull = N / kTmaScatterChunk;
+      if (!soa && aligned && sm <= 226 * 1024 && nfull > 0) {
+        auto k = bin_scatter_tma_kernel<D>;
+        cudaError_t e = allow_smem(k, sm);
+        if (e != cudaSuccess) return e;
+        const int blocks = (int)std::min<long long>(nfull, nsm);
+        k<<<blocks, kTmaScatterThreads, sm, s>>>(reinterpret_cast<const float*>(x), reinterpret_cast<const float*>(y),
+                                                 nfull, N, sg, cursor, reinterpret_cast<float*>(rec), err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long done = nfull * kTmaScatterChunk;
+        if (done < N) return scatter_sorted<D, TC, TV, TR>(x, y, soa, N, done, sg, cursor, rec, nsm, s);
+        return cudaSuccess;
+      }
+    }
+    return scatter_sorted<D, TC, TV, TR>(x, y, soa, N, 0, sg, cursor, rec, nsm, s);
   }
   const size_t sm = sg.ntiles <= kSmemBins ? sg.ntiles * (sizeof(long long) + sizeof(unsigned int)) : 0;
   auto k = bin_scatter_kernel<D, TC, TV, TR>;
@@ -834,12 +1317,13 @@ static cudaError_t scatter_d(const void* x, const void* y, int soa, long long N,
 }
 
 cudaError_t launch_bin_scatter(const void* x, int coord_f64, const void* y, int value_f64, int soa, long long N,
-                               const SortGeom& sg, int rec_f64, long long* cursor, void* rec, cudaStream_t s) {
+                               const SortGeom& sg, int rec_f64, long long* cursor, void* rec, int* err,
+                               cudaStream_t s) {
   if (N == 0) return cudaSuccess;
   const SortGeom& g = sg;
 #define EFGP_SC(DD, TC, TV)                                                                  \
-  return rec_f64 ? scatter_d<DD, TC, TV, double>(x, y, soa, N, g, cursor, rec, s)           \
-                 : scatter_d<DD, TC, TV, float>(x, y, soa, N, g, cursor, rec, s);
+  return rec_f64 ? scatter_d<DD, TC, TV, double>(x, y, soa, N, g, cursor, rec, err, s)      \
+                 : scatter_d<DD, TC, TV, float>(x, y, soa, N, g, cursor, rec, err, s);
 #define EFGP_SCD(DD)                                                \
   if (sg.d == DD) {                                                 \
     if (coord_f64 && value_f64) { EFGP_SC(DD, double, double) }     \
@@ -855,10 +1339,27 @@ cudaError_t launch_bin_scatter(const void* x, int coord_f64, const void* y, int 
 
 template <int D, int W, typename TR>
 static cudaError_t spread_dw(const void* rec, long long N, const SortGeom& sg, const long long* tile_off,
-                             const void* coef, double2* E, cudaStream_t s) {
+                             const void* coef, double2* E, int* err, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  constexpr bool use_tma = std::is_same<TR, float>::value && (D == 1 || (D == 2 && W <= 6));
+  if constexpr (use_tma) {
+    const size_t sm = spread_tma_smem(D, W);
+    if (sg.TB == RegTile<(D == 1 ? 1 : 2)>::TB && sm <= 226 * 1024 && sg.rstride % 4 == 0 &&
+        reinterpret_cast<uintptr_t>(rec) % 16 == 0) {
+      auto k = spread_tma_kernel<(D == 1 ? 1 : 2), W>;
+      cudaError_t e = allow_smem(k, sm);
+      if (e != cudaSuccess) return e;
+      long long nseg = (long long)nsm * 4;
+      long long seg = (N + nseg - 1) / nseg;
+      if (seg < kTmaSpreadBatch) seg = kTmaSpreadBatch;
+      nseg = (N + seg - 1) / seg;
+      k<<<(unsigned)nseg, kTmaSpreadThreads, sm, s>>>(reinterpret_cast<const float*>(rec), N, sg.rstride, sg, tile_off,
+                                                       seg, *reinterpret_cast<const EsCoef<float>*>(coef), E, err);
+      return cudaGetLastError();
+    }
+  }
   constexpr bool use_reg = std::is_same<TR, float>::value && (D == 1 || (D == 2 && W <= 7));
   if constexpr (use_reg) {
     if (sg.TB == RegTile<(D == 1 ? 1 : 2)>::TB) {
@@ -897,31 +1398,31 @@ static cudaError_t spread_dw(const void* rec, long long N, const SortGeom& sg, c
 
 template <int D, typename TR>
 static cudaError_t spread_d(const void* rec, long long N, const SortGeom& sg, const long long* tile_off,
-                            const void* coef, double2* E, cudaStream_t s) {
+                            const void* coef, double2* E, int* err, cudaStream_t s) {
   switch (sg.W) {
-    case 3: return spread_dw<D, 3, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 4: return spread_dw<D, 4, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 5: return spread_dw<D, 5, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 6: return spread_dw<D, 6, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 7: return spread_dw<D, 7, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 8: return spread_dw<D, 8, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 10: return spread_dw<D, 10, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 12: return spread_dw<D, 12, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 14: return spread_dw<D, 14, TR>(rec, N, sg, tile_off, coef, E, s);
-    case 16: return spread_dw<D, 16, TR>(rec, N, sg, tile_off, coef, E, s);
+    case 3: return spread_dw<D, 3, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 4: return spread_dw<D, 4, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 5: return spread_dw<D, 5, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 6: return spread_dw<D, 6, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 7: return spread_dw<D, 7, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 8: return spread_dw<D, 8, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 10: return spread_dw<D, 10, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 12: return spread_dw<D, 12, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 14: return spread_dw<D, 14, TR>(rec, N, sg, tile_off, coef, E, err, s);
+    case 16: return spread_dw<D, 16, TR>(rec, N, sg, tile_off, coef, E, err, s);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_spread(const void* rec, int rec_f64, long long N, const SortGeom& sg, const long long* tile_off,
-                          const void* coef, double2* E, cudaStream_t s) {
+                          const void* coef, double2* E, int* err, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  if (sg.d == 1) return rec_f64 ? spread_d<1, double>(rec, N, sg, tile_off, coef, E, s)
-                                : spread_d<1, float>(rec, N, sg, tile_off, coef, E, s);
-  if (sg.d == 2) return rec_f64 ? spread_d<2, double>(rec, N, sg, tile_off, coef, E, s)
-                                : spread_d<2, float>(rec, N, sg, tile_off, coef, E, s);
-  if (sg.d == 3) return rec_f64 ? spread_d<3, double>(rec, N, sg, tile_off, coef, E, s)
-                                : spread_d<3, float>(rec, N, sg, tile_off, coef, E, s);
+  if (sg.d == 1) return rec_f64 ? spread_d<1, double>(rec, N, sg, tile_off, coef, E, err, s)
+                                : spread_d<1, float>(rec, N, sg, tile_off, coef, E, err, s);
+  if (sg.d == 2) return rec_f64 ? spread_d<2, double>(rec, N, sg, tile_off, coef, E, err, s)
+                                : spread_d<2, float>(rec, N, sg, tile_off, coef, E, err, s);
+  if (sg.d == 3) return rec_f64 ? spread_d<3, double>(rec, N, sg, tile_off, coef, E, err, s)
+                                : spread_d<3, float>(rec, N, sg, tile_off, coef, E, err, s);
   return cudaErrorInvalidValue;
 }
 
