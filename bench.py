@@ -34,6 +34,41 @@ METRIC = "points/s end-to-end EFGP at stated mean error; spread/interp GB/s vs H
 UNIT = "points/s"
 
 
+KERNEL_SRC = os.path.join(ROOT, "paper_2210_10210_gb300", "csrc", "spread.cu")
+KERNEL_NAMES = {"spread": "spread_tma_kernel(", "bin_scatter": "bin_scatter_tma_kernel(",
+                "bin_count": "bin_count_kernel("}
+
+
+def kernel_fingerprint(key):
+    """SHA-1 of one kernel's source text (template header to closing brace);
+    DRAM counters recorded for another fingerprint are stale."""
+    text = open(KERNEL_SRC).read()
+    i = text.index(KERNEL_NAMES[key])
+    start = text.rfind("template", 0, i)
+    depth, j = 0, text.index("{", i)
+    while j < len(text):
+        if text[j] == "{":
+            depth += 1
+        elif text[j] == "}":
+            depth -= 1
+            if depth == 0:
+                break
+        j += 1
+    import hashlib
+    return hashlib.sha1(text[start:j + 1].encode()).hexdigest()
+
+
+def traffic_for(kernel, n_points, path):
+    """DRAM bytes per launch scaled from an ncu capture, or None when absent or stale."""
+    try:
+        t = json.load(open(path))["kernels"][kernel]
+    except Exception:
+        return None
+    if t.get("src_sha1") != kernel_fingerprint(kernel):
+        return None
+    return t["dram_bytes_per_point"] * n_points
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -186,7 +221,13 @@ def run_ours(args, rank, world):
     kern = E.Kernel(fam, nu, ell)
     prec = args.precision or ("fp64" if name == "se1d" else "mixed")
 
-    x, y = synthdata.make_torch(rec, dev)
+    if rec.cluster_frac > 0:       # clustered recipes are drawn on the host
+        xn, yn = synthdata.points_np(rec), None
+        yn = synthdata.values_np(rec, xn)
+        x, y = torch.from_numpy(xn).to(dev), torch.from_numpy(yn).to(dev)
+        del xn, yn
+    else:
+        x, y = synthdata.make_torch(rec, dev)
     z = torch.from_numpy(synthdata.targets_np(rec)).to(dev)
     q = z.shape[0]
     torch.cuda.synchronize()
@@ -200,6 +241,15 @@ def run_ours(args, rank, world):
         h.close()
         return info, mu, pt, par
 
+    if args.once:                     # one untimed pass (a target for profilers)
+        info, mu, pt, par = step()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"once": True, "workload": workload_desc(name, rec, model), "cg_iters": info["iters"],
+                              "launches": pt["launches"]}), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -250,11 +300,9 @@ def run_ours(args, rank, world):
     kt = tot[roof_kernel]
     achieved = alg[roof_kernel] / (kt / 1000.0) / 1e9 if kt > 0 else None
     traffic = None
-    if args.traffic_json and os.path.exists(args.traffic_json):
-        try:
-            traffic = json.load(open(args.traffic_json)).get(roof_kernel)
-        except Exception:
-            traffic = None
+    rk = roof_kernel.replace("_ms", "")
+    if rk in KERNEL_NAMES and args.traffic_json:
+        traffic = traffic_for(rk, rec.n, args.traffic_json)
     roofline = {"kernel": roof_kernel.replace("_ms", ""), "bound": "hbm", "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                 "peak_source": src, "alg_bytes_per_launch": alg[roof_kernel], "ms_per_launch": kt}
@@ -332,6 +380,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override the point count")
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--once", action="store_true", help="run one untimed step and exit (profiling target)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "traffic.json"))
     args = ap.parse_args()

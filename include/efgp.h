@@ -85,6 +85,8 @@ typedef struct {
   int iters_per_launch; /* CG iterations per captured CUDA graph launch (0: 32)           */
   int autotune;         /* 1: time candidate FFT line batches once per shape              */
   int profile;          /* 1: time each phase with CUDA events (efgp_get_phase_times)     */
+  int cg_mode;          /* 0: choose; 1: graph-captured kernels per iteration; 2: one   */
+                        /* persistent launch on a thread-block cluster (small problems)    */
   void* stream;         /* cudaStream_t to order work on (NULL: a private stream)         */
 } efgp_options;
 

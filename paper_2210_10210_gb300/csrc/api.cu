@@ -23,6 +23,8 @@ namespace efgp {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+bool error_empty() { return g_last_error.empty(); }
 
 bool fault_injected(const char* what) {
   const char* e = std::getenv("EFGP_FAULT");
@@ -35,9 +37,10 @@ namespace {
 
 #define EFGP_CK(call)                                                                          \
   do {                                                                                         \
+    efgp::clear_error();                                                                       \
     cudaError_t e_ = (call);                                                                   \
     if (e_ != cudaSuccess) {                                                                   \
-      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+      if (efgp::error_empty()) set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
       return e_ == cudaErrorMemoryAllocation ? EFGP_ENOMEM : EFGP_ECUDA;                       \
     }                                                                                          \
   } while (0)
@@ -639,6 +642,83 @@ int capture_cg_graph(efgp_handle* H) {
   return EFGP_OK;
 }
 
+
+// Persistent CG: line batches re-chosen for a 16-block cluster, problem
+// descriptor copied to the device once per handle.
+constexpr long long kPersistentMaxGrid = 1ll << 19;   // L^d above this: per-pass kernels
+constexpr size_t kPersistentMaxSmem = 160 * 1024;
+
+// batch: called for a batched solve (the automatic choice differs: a single
+// problem is faster with graph-captured per-pass kernels on the whole GPU)
+int persistent_prepare(efgp_handle* H, double rho, long long max_iter, bool batch) {
+  if (H->pcluster == 0) return EFGP_OK;
+  PersistentProblem& P = H->pprob;
+  if (H->pcluster < 0) {
+    const long long grid = ipow(H->par.L, H->d);
+    const int mode = H->opt.cg_mode;
+    if (mode == 1 || (mode == 0 && (grid > kPersistentMaxGrid || !batch)) || (int)H->mv.size() > kMaxPasses) {
+      H->pcluster = 0;
+      return EFGP_OK;
+    }
+    std::memset(&P, 0, sizeof(P));
+    P.npass = (int)H->mv.size();
+    // each cluster block takes at most one line batch per pass when shared
+    // memory allows (the passes are latency-bound: one round per phase)
+    auto fill = [&](int CL) -> size_t {
+      size_t smem = 0;
+      for (int q = 0; q < P.npass; ++q) {
+        const Pass& ps = H->mv[q];
+        LineGeom g = ps.g;
+        const long long lines = g.outer * g.inner;
+        g.nb = (int)std::max<long long>(1, (lines + CL - 1) / CL);
+        while (g.nb > 1 && line_fft_smem_bytes(g.L, g.nb, H->elem) > kPersistentMaxSmem) g.nb = (g.nb + 1) / 2;
+        smem = std::max(smem, line_fft_smem_bytes(g.L, g.nb, H->elem));
+        P.pass[q] = g;
+        P.inb[q] = ps.in_buf;
+        P.outb[q] = ps.out_buf;
+        P.dir[q] = ps.dir;
+        P.inm[q] = ps.inm;
+        P.outm[q] = ps.outm;
+        P.conv[q] = ps.conv ? 1 : 0;
+      }
+      return smem;
+    };
+    size_t smem = fill(16);
+    int cl = persistent_cluster_size(H->f64, smem);
+    cudaGetLastError();
+    if (cl == 8) {
+      smem = fill(8);
+      if (persistent_cluster_size(H->f64, smem) < 8) cl = 0;
+      cudaGetLastError();
+    }
+    if (cl == 0) {
+      H->pcluster = 0;
+      return EFGP_OK;
+    }
+    H->pcluster = cl;
+    H->psmem = smem;
+    P.buf[0] = nullptr;
+    P.buf[1] = H->scrA;
+    P.buf[2] = H->scrB;
+    P.tw = H->twL;
+    P.what = H->what;
+    P.x = H->x;
+    P.r = H->r;
+    P.p = H->p;
+    P.Ap = H->Ap;
+    P.b = H->b;
+    P.Dw = H->Dw;
+    P.sigma2 = H->sigma * H->sigma;
+    P.M = H->M;
+    P.st = H->st;
+    EFGP_TRY(H->alloc((void**)&H->d_pprob, sizeof(PersistentProblem)));
+  }
+  P.rho = rho;
+  P.max_iter = max_iter;
+  EFGP_CK(cudaMemcpyAsync(H->d_pprob, &P, sizeof(PersistentProblem), cudaMemcpyHostToDevice, H->stream));
+  return EFGP_OK;
+}
+
 int apply_system_dev(efgp_handle* H, double2* in, double2* out) {
   CgArgs cga{};
   cga.src = in;
@@ -840,11 +920,19 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   if (!H) return EFGP_EINVAL;
   const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
   const long long max_iter = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
-  EFGP_TRY(capture_cg_graph(H));
+  EFGP_TRY(persistent_prepare(H, rho, max_iter, false));
+  const bool persistent = H->pcluster > 0;
+  if (!persistent) EFGP_TRY(capture_cg_graph(H));
   cudaEvent_t e0, e1;
   EFGP_CK(cudaEventCreate(&e0));
   EFGP_CK(cudaEventCreate(&e1));
   EFGP_CK(cudaEventRecord(e0, H->stream));
+  if (persistent) {
+    EFGP_CK(launch_cg_persistent(H->d_pprob, 1, H->pcluster, H->psmem, H->f64, H->stream));
+    H->times.launches += 1;
+    EFGP_CK(cudaMemcpyAsync(H->host_state, H->st, sizeof(CgState), cudaMemcpyDeviceToHost, H->stream));
+    EFGP_CK(cudaStreamSynchronize(H->stream));
+  } else {
   EFGP_CK(launch_cg_init(H->b, H->x, H->r, H->p, H->M, rho, max_iter, H->st, H->partials, H->stream));
   H->times.launches += 1;
   long long launched = 0;
@@ -859,6 +947,7 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
       set_error("CG state never reported completion");
       return EFGP_ETIMEOUT;
     }
+  }
   }
   EFGP_CK(cudaEventRecord(e1, H->stream));
   const CgState st = *H->host_state;
@@ -1028,6 +1117,8 @@ int efgp_apply_system(efgp_handle* H, const double* in_host, double* out_host) {
 
 struct efgp_batch {
   std::vector<efgp_handle*> hs;
+  PersistentProblem* d_probs = nullptr;   // persistent descriptors of all problems
+  std::vector<PersistentProblem> h_probs;
   cudaStream_t main = nullptr;
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;
@@ -1091,6 +1182,65 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
   if (!B) return EFGP_EINVAL;
   const int n = (int)B->hs.size();
   for (efgp_handle* h : B->hs) EFGP_CK(cudaStreamSynchronize(h->stream));
+  // every problem small enough: one persistent launch, one cluster per problem
+  {
+    bool all = true;
+    int cl = 16, f64 = B->hs[0]->f64;
+    size_t smem = 0;
+    for (efgp_handle* H : B->hs) {
+      const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
+      const long long mi = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
+      EFGP_TRY(persistent_prepare(H, rho, mi, true));
+      all = all && H->pcluster > 0 && H->f64 == f64;
+      if (H->pcluster > 0) {
+        cl = std::min(cl, H->pcluster);
+        smem = std::max(smem, H->psmem);
+      }
+    }
+    if (all && persistent_cluster_size(f64, smem) >= cl) {
+      B->h_probs.resize(n);
+      for (int i = 0; i < n; ++i) B->h_probs[i] = B->hs[i]->pprob;
+      if (!B->d_probs) {
+        cudaError_t e = cudaMalloc((void**)&B->d_probs, sizeof(PersistentProblem) * n);
+        if (e != cudaSuccess) {
+          set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+          return EFGP_ENOMEM;
+        }
+      }
+      for (efgp_handle* H : B->hs) EFGP_CK(cudaStreamSynchronize(H->stream));
+      EFGP_CK(cudaMemcpyAsync(B->d_probs, B->h_probs.data(), sizeof(PersistentProblem) * n, cudaMemcpyHostToDevice,
+                              B->main));
+      cudaEvent_t e0, e1;
+      EFGP_CK(cudaEventCreate(&e0));
+      EFGP_CK(cudaEventCreate(&e1));
+      EFGP_CK(cudaEventRecord(e0, B->main));
+      EFGP_CK(launch_cg_persistent(B->d_probs, n, cl, smem, f64, B->main));
+      EFGP_CK(cudaEventRecord(e1, B->main));
+      for (int i = 0; i < n; ++i)
+        EFGP_CK(cudaMemcpyAsync(&B->host_states[i], B->hs[i]->st, sizeof(CgState), cudaMemcpyDeviceToHost, B->main));
+      EFGP_CK(cudaStreamSynchronize(B->main));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      int rc = EFGP_OK;
+      for (int i = 0; i < n; ++i) {
+        efgp_handle* H = B->hs[i];
+        H->solved = true;
+        H->times.launches += 1;
+        const CgState& st = B->host_states[i];
+        if (info) {
+          info[i].iters = st.iter;
+          info[i].rel_residual = st.bnorm2 > 0 ? std::sqrt(st.rr / st.bnorm2) : 0.0;
+          info[i].true_rel_residual = -1.0;
+          info[i].converged = st.done == 1;
+          info[i].solve_ms = ms;
+        }
+        if (st.done != 1 && rc == EFGP_OK) rc = st.done == 3 ? EFGP_ECUDA : EFGP_ENOTCONV;
+      }
+      return rc;
+    }
+  }
   const int iters = B->hs[0]->opt.iters_per_launch > 0 ? B->hs[0]->opt.iters_per_launch : 32;
   long long max_iter = 0;
   for (efgp_handle* h : B->hs) max_iter = std::max<long long>(max_iter, h->opt.max_iter > 0 ? h->opt.max_iter : 100000);
@@ -1201,6 +1351,7 @@ void efgp_batch_destroy(efgp_batch* B) {
   if (!B) return;
   if (B->main) cudaStreamSynchronize(B->main);
   for (efgp_handle* h : B->hs) efgp_destroy(h);
+  if (B->d_probs) cudaFree(B->d_probs);
   if (B->graph) cudaGraphExecDestroy(B->graph);
   for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
   for (cudaStream_t s : B->side) cudaStreamDestroy(s);

@@ -54,6 +54,34 @@ __device__ __forceinline__ void es_weights(T f, const EsCoef<T>& cf, T (&wt)[W])
   }
 }
 
+// The same weights with pairs of pieces evaluated by packed two-lane FP32
+// FMAs (one instruction for two pieces).
+template <int W>
+__device__ __forceinline__ void es_weights_x2(float f, const EsCoef<float>& cf, float (&wt)[W]) {
+  constexpr int DEG = es_degree(W);
+  constexpr int NP = W / 2;
+  const float t = 2.f * f - 1.f;
+  const float2 tt = make_float2(t, t);
+  float2 acc[NP > 0 ? NP : 1];
+  float last = 0.f;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) acc[j] = make_float2(cf.c[DEG * W + 2 * j], cf.c[DEG * W + 2 * j + 1]);
+  if (W & 1) last = cf.c[DEG * W + W - 1];
+#pragma unroll
+  for (int k = DEG - 1; k >= 0; --k) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j)
+      acc[j] = __ffma2_rn(acc[j], tt, make_float2(cf.c[k * W + 2 * j], cf.c[k * W + 2 * j + 1]));
+    if (W & 1) last = fmaf(last, t, cf.c[k * W + W - 1]);
+  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    wt[2 * j] = acc[j].x;
+    wt[2 * j + 1] = acc[j].y;
+  }
+  if (W & 1) wt[W - 1] = last;
+}
+
 // Fine-grid position of a coordinate x in [0,1]: u = x * s, footprint start
 // l0 = ceil(u - W/2), offset f = l0 - (u - W/2) in [0,1).
 struct GridScale {

@@ -32,6 +32,8 @@ constexpr int es_degree(int w) { return w + 2; }
 constexpr int tile_edge(int d) { return d == 1 ? 256 : (d == 2 ? 16 : 8); }
 
 void set_error(const std::string& msg);
+void clear_error();
+bool error_empty();
 
 // ---------------------------------------------------------------------------
 // Host-side planning (host_params.cpp).  All FP64.

@@ -19,169 +19,9 @@
 #include <cstdio>
 
 #include "kernels.h"
+#include "line_fft.cuh"
 
 namespace efgp {
-
-// ------------------------------------------------------------ small DFTs
-template <typename T, int R> struct Roots;
-template <typename T> struct Roots<T, 3> {
-  static __device__ __forceinline__ T c(int k) { return k == 0 ? T(1) : T(-0.5); }
-  static __device__ __forceinline__ T s(int k) {
-    return k == 0 ? T(0) : (k == 1 ? T(0.86602540378443864676) : T(-0.86602540378443864676));
-  }
-};
-template <typename T> struct Roots<T, 5> {
-  static __device__ __forceinline__ T c(int k) {
-    const T t[5] = {T(1), T(0.30901699437494742410), T(-0.80901699437494742410), T(-0.80901699437494742410),
-                    T(0.30901699437494742410)};
-    return t[k];
-  }
-  static __device__ __forceinline__ T s(int k) {
-    const T t[5] = {T(0), T(0.95105651629515357212), T(0.58778525229247312917), T(-0.58778525229247312917),
-                    T(-0.95105651629515357212)};
-    return t[k];
-  }
-};
-template <typename T> struct Roots<T, 7> {
-  static __device__ __forceinline__ T c(int k) {
-    const T t[7] = {T(1),
-                    T(0.62348980185873353053),
-                    T(-0.22252093395631440429),
-                    T(-0.90096886790241912624),
-                    T(-0.90096886790241912624),
-                    T(-0.22252093395631440429),
-                    T(0.62348980185873353053)};
-    return t[k];
-  }
-  static __device__ __forceinline__ T s(int k) {
-    const T t[7] = {T(0),
-                    T(0.78183148246802980871),
-                    T(0.97492791218182360702),
-                    T(0.43388373911755812048),
-                    T(-0.43388373911755812048),
-                    T(-0.97492791218182360702),
-                    T(-0.78183148246802980871)};
-    return t[k];
-  }
-};
-
-// out[q] = sum_r v[r] exp(dir 2 pi i r q / R), in place.
-template <typename T, int R>
-__device__ __forceinline__ void dft_generic(cplx<T>* v, int dir) {
-  cplx<T> o[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    T re = 0, im = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int k = (r * q) % R;
-      const T c = Roots<T, R>::c(k), s = dir * Roots<T, R>::s(k);
-      re += v[r].x * c - v[r].y * s;
-      im += v[r].x * s + v[r].y * c;
-    }
-    o[q] = mk<T>(re, im);
-  }
-#pragma unroll
-  for (int q = 0; q < R; ++q) v[q] = o[q];
-}
-
-template <typename T>
-__device__ __forceinline__ void dft2(cplx<T>& a, cplx<T>& b) {
-  cplx<T> t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
-}
-
-template <typename T>
-__device__ __forceinline__ void dft4(cplx<T>* v, int dir) {
-  cplx<T> a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-  cplx<T> c = cadd(v[1], v[3]), d = cmul_si(csub(v[1], v[3]), dir);
-  v[0] = cadd(a, c);
-  v[2] = csub(a, c);
-  v[1] = cadd(b, d);
-  v[3] = csub(b, d);
-}
-
-template <typename T>
-__device__ __forceinline__ void dft8(cplx<T>* v, int dir) {
-  cplx<T> e[4] = {v[0], v[2], v[4], v[6]};
-  cplx<T> o[4] = {v[1], v[3], v[5], v[7]};
-  dft4<T>(e, dir);
-  dft4<T>(o, dir);
-  const T h = T(0.70710678118654752440);
-  // o[q] *= exp(dir 2 pi i q / 8)
-  o[1] = mk<T>(h * (o[1].x - dir * o[1].y), h * (o[1].y + dir * o[1].x));
-  o[2] = cmul_si(o[2], dir);
-  o[3] = mk<T>(h * (-o[3].x - dir * o[3].y), h * (-o[3].y + dir * o[3].x));
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    v[q] = cadd(e[q], o[q]);
-    v[q + 4] = csub(e[q], o[q]);
-  }
-}
-
-template <typename T, int R>
-__device__ __forceinline__ void dft(cplx<T>* v, int dir) {
-  if constexpr (R == 2) dft2<T>(v[0], v[1]);
-  else if constexpr (R == 4) dft4<T>(v, dir);
-  else if constexpr (R == 8) dft8<T>(v, dir);
-  else dft_generic<T, R>(v, dir);
-}
-
-// One radix-R Stockham pass over nb lines in shared memory.
-template <typename T, int R>
-__device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst, int L,
-                                              int LP, int nb, int Ns, int dir, const cplx<T>* __restrict__ tw) {
-  const int nbf = L / R;
-  const int tstride = L / (Ns * R);
-  for (int bidx = threadIdx.x; bidx < nb * nbf; bidx += blockDim.x) {
-    const int li = bidx / nbf;
-    const int j = bidx - li * nbf;
-    const int k = j % Ns;
-    const cplx<T>* s = src + li * LP;
-    cplx<T> v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
-    if (Ns > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        cplx<T> t = __ldg(tw + k * r * tstride);
-        if (dir > 0) t.y = -t.y;
-        v[r] = cmul(v[r], t);
-      }
-    }
-    dft<T, R>(v, dir);
-    cplx<T>* d = dst + li * LP + (j / Ns) * Ns * R + k;
-#pragma unroll
-    for (int r = 0; r < R; ++r) d[r * Ns] = v[r];
-  }
-}
-
-// Full transform of nb lines; returns the buffer holding the result.
-template <typename T>
-__device__ cplx<T>* stockham_all(cplx<T>* b0, cplx<T>* b1, const LineGeom& g, int LP, int nb, int dir,
-                                 const cplx<T>* tw) {
-  int Ns = 1;
-  cplx<T>* src = b0;
-  cplx<T>* dst = b1;
-  for (int p = 0; p < g.npass; ++p) {
-    const int R = g.radix[p];
-    switch (R) {
-      case 2: stockham_pass<T, 2>(src, dst, g.L, LP, nb, Ns, dir, tw); break;
-      case 3: stockham_pass<T, 3>(src, dst, g.L, LP, nb, Ns, dir, tw); break;
-      case 4: stockham_pass<T, 4>(src, dst, g.L, LP, nb, Ns, dir, tw); break;
-      case 5: stockham_pass<T, 5>(src, dst, g.L, LP, nb, Ns, dir, tw); break;
-      case 7: stockham_pass<T, 7>(src, dst, g.L, LP, nb, Ns, dir, tw); break;
-      default: stockham_pass<T, 8>(src, dst, g.L, LP, nb, Ns, dir, tw); break;
-    }
-    __syncthreads();
-    cplx<T>* t = src;
-    src = dst;
-    dst = t;
-    Ns *= R;
-  }
-  return src;
-}
 
 template <typename T, int INM, int OUTM, bool CONV>
 __global__ void __launch_bounds__(256) line_fft_kernel(LineGeom g, const void* __restrict__ in_v, void* out_v, int dir,
@@ -192,88 +32,9 @@ __global__ void __launch_bounds__(256) line_fft_kernel(LineGeom g, const void* _
   if (INM == IN_CG || OUTM == OUT_CG) {
     if (cga.check_done && cga.st->done) return;
   }
-  const int L = g.L, nb = g.nb;
-  const int LP = L + 1;
-  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* b1 = b0 + (size_t)nb * LP;
-  const long long nlines = g.outer * g.inner;
-  const long long line0 = (long long)blockIdx.x * nb;
-  const bool strided = g.inner > 1;
-
-  // ---- load (zero-padded to L)
   double cg_beta = 0.0;
   if (INM == IN_CG && cga.update_p) cg_beta = cga.st->beta;
-  for (int e = threadIdx.x; e < nb * L; e += blockDim.x) {
-    int li, k;
-    if (strided) { li = e % nb; k = e / nb; } else { li = e / L; k = e - li * L; }
-    const long long line = line0 + li;
-    cplx<T> v = mk<T>(0, 0);
-    if (line < nlines && k < g.n_in) {
-      const long long o = line / g.inner, i = line - o * g.inner;
-      if (INM == IN_PLAIN) {
-        v = reinterpret_cast<const cplx<T>*>(in_v)[o * g.in_so + (long long)k * g.in_sk + i * g.in_si];
-      } else {
-        const long long j = o * g.n_in + k;   // flat index into the M-vector
-        double2 pv = cga.src[j];
-        if (cga.update_p) {
-          const double2 rv = cga.r[j];
-          pv.x = rv.x + cg_beta * pv.x;
-          pv.y = rv.y + cg_beta * pv.y;
-          cga.src[j] = pv;
-        }
-        const double dj = cga.Dw[j];
-        v = mk<T>((T)(dj * pv.x), (T)(dj * pv.y));
-      }
-    }
-    b0[li * LP + k] = v;
-  }
-  __syncthreads();
-
-  cplx<T>* res;
-  if (CONV) {
-    res = stockham_all<T>(b0, b1, g, LP, nb, -1, tw);
-    // pointwise product with the (real) transformed generating vector
-    for (int e = threadIdx.x; e < nb * L; e += blockDim.x) {
-      int li, k;
-      if (strided) { li = e % nb; k = e / nb; } else { li = e / L; k = e - li * L; }
-      const long long line = line0 + li;
-      if (line < nlines) {
-        const long long o = line / g.inner, i = line - o * g.inner;
-        const T wv = __ldg(what + (o * L + k) * g.inner + i);
-        cplx<T> t = res[li * LP + k];
-        res[li * LP + k] = mk<T>(t.x * wv, t.y * wv);
-      }
-    }
-    __syncthreads();
-    cplx<T>* other = (res == b0) ? b1 : b0;
-    res = stockham_all<T>(res, other, g, LP, nb, +1, tw);
-  } else {
-    res = stockham_all<T>(b0, b1, g, LP, nb, dir, tw);
-  }
-
-  // ---- store the first n_out entries
-  double dot = 0.0;
-  for (int e = threadIdx.x; e < nb * g.n_out; e += blockDim.x) {
-    int li, k;
-    if (strided) { li = e % nb; k = e / nb; } else { li = e / g.n_out; k = e - li * g.n_out; }
-    const long long line = line0 + li;
-    if (line >= nlines) continue;
-    const long long o = line / g.inner, i = line - o * g.inner;
-    const cplx<T> v = res[li * LP + k];
-    if (OUTM == OUT_PLAIN) {
-      reinterpret_cast<cplx<T>*>(out_v)[o * g.out_so + (long long)k * g.out_sk + i * g.out_si] = v;
-    } else {
-      const long long j = o * g.n_out + k;
-      const double dj = cga.Dw[j];
-      const double2 sv = cga.src[j];
-      double2 a;
-      a.x = dj * (double)v.x + cga.sigma2 * sv.x;
-      a.y = dj * (double)v.y + cga.sigma2 * sv.y;
-      cga.dst[j] = a;
-      dot += sv.x * a.x + sv.y * a.y;   // Re(conj(src) * a)
-    }
-  }
-
+  const double dot = line_block<T, INM, OUTM, CONV>(g, blockIdx.x, in_v, out_v, dir, tw, what, cga, cg_beta, smem_raw);
   if (OUTM == OUT_CG && cga.do_dot) {
     const double bs = block_sum(dot, red);
     __shared__ bool last;

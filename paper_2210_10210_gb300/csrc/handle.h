@@ -78,6 +78,11 @@ struct efgp_handle {
   bool solved = false;
   std::vector<void*> allocs;
   efgp_phase_times times{};
+  // persistent CG (one launch on a thread-block cluster)
+  int pcluster = -1;                    // -1 undecided, 0 not eligible, else cluster size
+  size_t psmem = 0;
+  efgp::PersistentProblem pprob{};
+  efgp::PersistentProblem* d_pprob = nullptr;
   cudaEvent_t ev[8] = {};
   bool ev_made = false;
 

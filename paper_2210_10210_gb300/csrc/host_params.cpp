@@ -308,7 +308,7 @@ int plan_nufft(int d, int K, double h, double tol, double cost_points, double up
                NufftPlan* out) {
   std::vector<double> qx, qw;
   gauss_legendre(96, qx, qw);
-  std::vector<double> sigmas = {1.5, 2.0, 2.5, 3.0};
+  std::vector<double> sigmas = {1.5, 2.0, 2.5, 3.0, 4.0};
   if (upsamp_override > 0) sigmas = {upsamp_override};
   double best = std::numeric_limits<double>::infinity();
   bool found = false;

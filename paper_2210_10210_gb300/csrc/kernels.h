@@ -38,6 +38,29 @@ constexpr int kLineFftMaxSmem = 200 * 1024;   // dynamic shared memory cap of on
 template <typename T>
 cudaError_t prepare_line_fft();
 
+// ---- persistent CG on one thread-block cluster per problem (cg_persistent.cu)
+constexpr int kMaxPasses = 5;
+constexpr int kPersistentThreads = 256;
+struct PersistentProblem {
+  LineGeom pass[kMaxPasses];
+  int npass;
+  int inb[kMaxPasses], outb[kMaxPasses], dir[kMaxPasses], inm[kMaxPasses], outm[kMaxPasses], conv[kMaxPasses];
+  void* buf[3];          // buffer ids of the passes: 0 unused, 1 and 2 scratch
+  const void* tw;        // twiddles of length L (grid precision)
+  const void* what;      // transformed generating vector (grid precision)
+  double2 *x, *r, *p, *Ap;
+  const double2* b;
+  const double* Dw;
+  double sigma2;
+  long long M;
+  double rho;
+  long long max_iter;
+  CgState* st;           // final state written here
+};
+cudaError_t launch_cg_persistent(const PersistentProblem* d_probs, int nprob, int cluster, size_t smem, int f64,
+                                 cudaStream_t s);
+int persistent_cluster_size(int f64, size_t smem);
+
 // ---- CG vector kernels (cg.cu)
 cudaError_t launch_cg_init(const double2* b, double2* x, double2* r, double2* p, long long M, double rho,
                            long long max_iter, CgState* st, double* partials, cudaStream_t s);

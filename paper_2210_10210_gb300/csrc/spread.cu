@@ -6,6 +6,7 @@
 // w = conj v) and the right-hand side D F^* y (eq. rhs).
 #include <cmath>
 #include <cstdio>
+#include <string>
 #include <type_traits>
 
 #include "kernels.h"
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kSortThreads) bin_count_kernel(const TC* __res
                                                                  SortGeom sg, unsigned int* __restrict__ counts,
                                                                  int* range_flag) {
   extern __shared__ unsigned int hist[];
-  constexpr int U = 4;   // points per thread per step: keeps several loads in flight
+  constexpr int U = 8;   // points per thread per step: keeps several loads in flight
   const bool sm = sg.ntiles <= kSmemBins;
   if (sm) {
     for (int i = threadIdx.x; i < sg.ntiles; i += blockDim.x) hist[i] = 0u;
@@ -890,9 +891,9 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
       r /= TB;
     }
   }
-  float are[FP], aim[FP];
+  float2 acc[FP];   // (strength 1, strength y) per footprint cell
 #pragma unroll
-  for (int i = 0; i < FP; ++i) are[i] = aim[i] = 0.f;
+  for (int i = 0; i < FP; ++i) acc[i] = make_float2(0.f, 0.f);
 
   int abort_it = -1;
   for (int it = 0;; ++it) {
@@ -976,24 +977,19 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
       for (int j = half; j < c_n; j += 2) {
         const int k = idx[c_s + j];
         float w0[W], w1[W];
-        es_weights<float, W>(sq0[k] - (float)own[0], cf, w0);
+        es_weights_x2<W>(sq0[k] - (float)own[0], cf, w0);
         const float yv = sy[k];
+        const float2 c2 = make_float2(1.f, yv);
         if (D == 1) {
 #pragma unroll
-          for (int u = 0; u < W; ++u) {
-            are[u] += w0[u];
-            aim[u] = fmaf(w0[u], yv, aim[u]);
-          }
+          for (int u = 0; u < W; ++u) acc[u] = __ffma2_rn(make_float2(w0[u], w0[u]), c2, acc[u]);
         } else {
-          es_weights<float, W>(sq1[k] - (float)own[D - 1], cf, w1);
+          es_weights_x2<W>(sq1[k] - (float)own[D - 1], cf, w1);
 #pragma unroll
           for (int u = 0; u < W; ++u) {
-            const float wa = w0[u], wy = w0[u] * yv;
+            const float2 wa = __fmul2_rn(make_float2(w0[u], w0[u]), c2);
 #pragma unroll
-            for (int v = 0; v < W; ++v) {
-              are[u * W + v] = fmaf(wa, w1[v], are[u * W + v]);
-              aim[u * W + v] = fmaf(wy, w1[v], aim[u * W + v]);
-            }
+            for (int v = 0; v < W; ++v) acc[u * W + v] = __ffma2_rn(wa, make_float2(w1[v], w1[v]), acc[u * W + v]);
           }
         }
       }
@@ -1011,14 +1007,14 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
             int cc;
             if (D == 1) cc = own[0] + i;
             else cc = (own[0] + i / W) * S + own[D - 1] + i % W;
-            tile[2 * cc] += are[i];
-            tile[2 * cc + 1] += aim[i];
+            tile[2 * cc] += acc[i].x;
+            tile[2 * cc + 1] += acc[i].y;
           }
           __syncthreads();
         }
       }
 #pragma unroll
-      for (int i = 0; i < FP; ++i) are[i] = aim[i] = 0.f;
+      for (int i = 0; i < FP; ++i) acc[i] = make_float2(0.f, 0.f);
       int tcv[2] = {0, 0};
       {
         int r = tt;
@@ -1219,9 +1215,11 @@ static int grid_for(long long n, int threads, int cap = 4096) {
   return (int)b;
 }
 
+// Opt the kernel in to `bytes` of dynamic shared memory (needed above the
+// 48 KB default; static shared memory counts against that default too).
 template <typename K>
 static cudaError_t allow_smem(K kern, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  if (bytes <= 32 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -1271,11 +1269,18 @@ static cudaError_t scatter_sorted(const void* x, const void* y, int soa, long lo
                     2 * sizeof(int) * sg.ntiles;
   auto k = bin_scatter_sorted_kernel<D, TC, TV, TR, PPT>;
   cudaError_t e = allow_smem(k, sm);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    set_error("sorting scatter: shared-memory opt-in of " + std::to_string(sm) + " bytes failed");
+    return e;
+  }
   const int blocks = grid_for(N - n_begin, P, nsm * 4);
   k<<<blocks, 256, sm, s>>>(reinterpret_cast<const TC*>(x), reinterpret_cast<const TV*>(y), soa, N, n_begin, sg,
                             cursor, reinterpret_cast<TR*>(rec));
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess)
+    set_error("sorting scatter launch (" + std::to_string(blocks) + " blocks, " + std::to_string(sm) +
+              " bytes): " + cudaGetErrorString(e));
+  return e;
 }
 
 template <int D, typename TC, typename TV, typename TR>
@@ -1293,12 +1298,20 @@ static cudaError_t scatter_d(const void* x, const void* y, int soa, long long N,
       if (!soa && aligned && sm <= 226 * 1024 && nfull > 0) {
         auto k = bin_scatter_tma_kernel<D>;
         cudaError_t e = allow_smem(k, sm);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+          set_error("bulk-copy scatter: shared-memory opt-in of " + std::to_string(sm) + " bytes failed: " +
+                    cudaGetErrorString(e));
+          return e;
+        }
         const int blocks = (int)std::min<long long>(nfull, nsm);
         k<<<blocks, kTmaScatterThreads, sm, s>>>(reinterpret_cast<const float*>(x), reinterpret_cast<const float*>(y),
                                                  nfull, N, sg, cursor, reinterpret_cast<float*>(rec), err);
         e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) {
+          set_error("bulk-copy scatter launch (" + std::to_string(blocks) + " blocks, " + std::to_string(sm) +
+                    " bytes): " + cudaGetErrorString(e));
+          return e;
+        }
         const long long done = nfull * kTmaScatterChunk;
         if (done < N) return scatter_sorted<D, TC, TV, TR>(x, y, soa, N, done, sg, cursor, rec, nsm, s);
         return cudaSuccess;

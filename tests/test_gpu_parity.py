@@ -144,6 +144,28 @@ def test_toeplitz_apply_matches_dense(E):
         h.close()
 
 
+@pytest.mark.parametrize("name,n,prec", [("matern2d", 100_000, "mixed"), ("se3d", 50_000, "mixed"),
+                                         ("se1d", 10_000, "fp64"), ("matern2d", 20_000, "fp64")])
+def test_persistent_cluster_cg_matches_graph_cg(E, name, n, prec):
+    # one persistent launch on a thread-block cluster vs graph-captured
+    # per-pass kernels: same iterations up to rounding, same mean
+    rec = synthdata.config(name, n=n)
+    x, y, z = synthdata.make_np(rec)
+    z = z[:5000]
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS[name])
+    out = {}
+    for mode in (1, 2):
+        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, precision=prec, cg_mode=mode)
+        info = h.solve()
+        assert info["converged"], (mode, info)
+        out[mode] = (info, h.predict(_dev(z)).double().cpu().numpy())
+        h.close()
+    (i1, m1), (i2, m2) = out[1], out[2]
+    assert abs(i1["iters"] - i2["iters"]) <= max(3, 0.05 * i1["iters"])
+    assert np.abs(m1 - m2).max() <= 0.2 * 10 * eps * np.abs(y).max()
+    assert i2["true_rel_residual"] <= 10 * eps
+
+
 def test_ragged_tiny_and_edge_points(E):
     ek, ok, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
     rng = np.random.default_rng(5)
