@@ -222,6 +222,42 @@ def direct_type1(x: np.ndarray, c: np.ndarray, h: float, K: int, chunk: int = 20
     return out
 
 
+def direct_modes(x, c, h: float, ks, chunk: int = 4_000_000, threads: int = 0) -> np.ndarray:
+    """sum_n c_n exp(-2 pi i h k.x_n) for each listed multi-index k (rows of ks).
+
+    The same direct sum as direct_type1, for a few modes over very many points:
+    the points are visited in chunks (numpy releases the interpreter lock in
+    its array loops, so chunks run on several threads); each chunk's sums are
+    added in chunk order, so the result does not depend on the thread count.
+    """
+    import concurrent.futures as cf
+    import os
+    x = np.asarray(x)
+    if x.ndim == 1:
+        x = x[:, None]
+    ks = np.atleast_2d(np.asarray(ks, np.float64))
+    n = x.shape[0]
+    scalar_c = np.isscalar(c)
+
+    def part(s):
+        xs = x[s:s + chunk].astype(np.float64)
+        cs = 1.0 if scalar_c else np.asarray(c[s:s + chunk], np.float64)
+        ph = -2.0 * math.pi * h * (xs @ ks.T)          # (chunk, nk)
+        cr = np.cos(ph)
+        ci = np.sin(ph)
+        if scalar_c:
+            return cr.sum(0) + 1j * ci.sum(0)
+        return cs @ cr + 1j * (cs @ ci)
+    starts = list(range(0, n, chunk))
+    nthreads = threads or min(16, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(nthreads) as ex:
+        parts = list(ex.map(part, starts))
+    out = np.zeros(ks.shape[0], np.complex128)
+    for p_ in parts:
+        out += p_ * (c if scalar_c else 1.0)
+    return out
+
+
 def toeplitz_vector(x, h: float, m: int) -> np.ndarray:
     """w_k = sum_n exp(-2 pi i h k.x_n), k in J_{2m} (eq. 88, sign reading above)."""
     x = np.asarray(x, np.float64)

@@ -1,0 +1,79 @@
+"""Parity at the billion-point workload's full size, in the bench's launch
+configuration (default options, device inputs).
+
+The oracle cannot form all (4m+1)^2 Toeplitz entries from 1e9 points, so it
+checks what it can compute one by one: sampled entries of w (eq. 88) and
+b = D F^* y (eq. rhs) by direct sums over all 1e9 points; then, from the
+GPU's own (verified) w and b, the dense Cholesky solution and the direct
+posterior mean at sampled targets, which must match the GPU's CG + type-2
+mean to 10 eps max|y|.
+"""
+import numpy as np
+import pytest
+
+import synthdata
+from oracle import efgp_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_10210_gb300 as E
+    from paper_2210_10210_gb300 import build
+    build.build()
+    return E
+
+
+def test_billion_point_workload_sampled_parity(E):
+    name = "matern2d_1e9"
+    rec = synthdata.config(name)
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    x, y = synthdata.make_torch(rec, "cuda")
+    z = torch.from_numpy(synthdata.targets_np(rec)).cuda()
+    h = E.setup(x, y, E.Kernel(fam, nu, ell), sigma, eps)
+    info = h.solve()
+    mu = h.predict(z).double().cpu().numpy()
+    w, b = h.system()
+    par = h.params()
+    h.close()
+    assert info["converged"]
+    xh = x.cpu().numpy()
+    yh = y.cpu().numpy()
+    del x, y
+    torch.cuda.empty_cache()
+    n = xh.shape[0]
+    okern = O.Kernel(fam, nu, ell)
+    hh, m = O.choose_h_m(okern, 2, eps)
+    assert m == par["m"] and abs(hh - par["h"]) < 1e-12
+    D = O.spectral_weights(okern, 2, hh, m)
+    tol = eps / 10
+    rng = np.random.default_rng(2024)
+
+    # sampled Toeplitz entries over all points
+    kw = np.array([[0, 0], [2 * m, -2 * m], [1, 0], [-m, 3]] +
+                  [list(rng.integers(-2 * m, 2 * m + 1, 2)) for _ in range(3)])
+    wd = O.direct_modes(xh, 1.0, hh, kw)
+    for k, ref in zip(kw, wd):
+        assert abs(w[k[0] + 2 * m, k[1] + 2 * m] - ref) <= 3 * tol * n, (k, w[k[0] + 2 * m, k[1] + 2 * m], ref)
+    # sampled right-hand-side entries
+    kb = np.array([[0, 0], [m, -m], [-1, 2]] + [list(rng.integers(-m, m + 1, 2)) for _ in range(2)])
+    bd = O.direct_modes(xh, yh, hh, kb)
+    ysum = float(np.abs(yh).sum(dtype=np.float64))
+    for k, ref in zip(kb, bd):
+        j = (k[0] + m) * (2 * m + 1) + (k[1] + m)
+        assert abs(b[j] / D[j] - ref) <= 3 * tol * ysum, (k, b[j] / D[j], ref)
+
+    # the solve and the mean at sampled targets, from the GPU's own system
+    A = O.system_matrix(w, D, sigma, m, 2)
+    beta = O.solve_weights(A, b)
+    del A
+    zs_idx = rng.choice(mu.shape[0], 2000, replace=False)
+    zs = synthdata.targets_np(rec)[zs_idx]
+    ref_mu = O.mean_at(zs, beta, D, hh, m).real
+    ymax = float(np.abs(yh).max())
+    err = np.abs(mu[zs_idx] - ref_mu).max()
+    assert err <= 10 * eps * ymax, (err, 10 * eps * ymax)

@@ -184,6 +184,22 @@ def test_type1_brute_force_3d():
         assert abs(got[i, j, l] - want) <= 1e-12 * np.abs(c).sum()
 
 
+def test_direct_modes_agree_with_direct_type1():
+    # the few-mode, many-point direct sum against the lattice-pinned full sum
+    rng = np.random.default_rng(9)
+    x = rng.random((5000, 2)).astype(np.float32)
+    y = rng.standard_normal(5000).astype(np.float32)
+    h, K = 0.7, 6
+    full_w = O.direct_type1(x, np.ones(5000), h, K)
+    full_b = O.direct_type1(x, y, h, K)
+    ks = np.array([[0, 0], [3, -2], [-6, 6], [1, 5]])
+    got_w = O.direct_modes(x, 1.0, h, ks, chunk=777, threads=3)
+    got_b = O.direct_modes(x, y, h, ks, chunk=1000, threads=2)
+    for i, (a, b) in enumerate(ks):
+        assert abs(got_w[i] - full_w[a + K, b + K]) <= 1e-10 * 5000
+        assert abs(got_b[i] - full_b[a + K, b + K]) <= 1e-10 * np.abs(y).sum()
+
+
 # ---------------------------------------------------------------- structure and solve
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_dense_PhiStarPhi_equals_toeplitz_assembly(d):
