@@ -138,6 +138,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_rank, world, ms_per_step):
+    """Whole-job points/s: every rank's points over the slowest rank's step time."""
+    return world * points_per_rank / (ms_per_step / 1000.0)
+
+
+def rank_recipe(name, n, rank):
+    """The workload of one rank: same shape, its own seed (independent problems)."""
+    rec = synthdata.config(name, n=n)
+    rec.seed += 1000 * rank
+    return rec
+
+
 def workload_desc(name, rec, model):
     fam, nu, ell, sigma, eps = model
     kern = "SE" if fam == "se" else f"Matern-{nu:g}"
@@ -214,8 +236,7 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl", device_id=dev)
 
     name = args.config
-    rec = synthdata.config(name, n=args.n)
-    rec.seed += 1000 * rank                  # independent problem per rank
+    rec = rank_recipe(name, args.n, rank)    # independent problem per rank
     model = synthdata.MODELS[name]
     fam, nu, ell, sigma, eps = model
     kern = E.Kernel(fam, nu, ell)
@@ -268,13 +289,9 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     ms_step = ms / args.steps
-    value = world * rec.n / (ms_step / 1000.0)
+    value = job_throughput(rec.n, world, ms_step)
 
     # phase shares and the dominant kernel's roofline
     keys = ["bin_count_ms", "bin_scatter_ms", "spread_ms", "fine_fft_ms", "what_ms", "cg_ms", "predict_fft_ms",
@@ -335,12 +352,8 @@ def run_ours(args, rank, world):
         for _ in range(ke):
             e2e_step()
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / ke
-        if dist:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * rec.n / te, "unit": UNIT,
+        te = max_over_ranks((time.perf_counter() - t0) / ke, dist, dev)
+        e2e = {"value": job_throughput(rec.n, world, 1000 * te), "unit": UNIT,
                "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes + zn.nbytes), "d2h_bytes_per_step": int(mu_h.nbytes),
                "ms_per_step": 1000 * te}
 

@@ -11,8 +11,10 @@ namespace efgp {
 
 constexpr int kCgThreads = 256;
 
+// One element per thread up to 1024 blocks: the FP64 vector arithmetic is
+// spread over as many SMs as the vector allows (FP64 throughput per SM is low).
 int cg_blocks(long long M) {
-  long long b = (M + kCgThreads * 4 - 1) / (kCgThreads * 4);
+  long long b = (M + kCgThreads - 1) / kCgThreads;
   if (b < 1) b = 1;
   if (b > 1024) b = 1024;
   return (int)b;
@@ -63,6 +65,7 @@ __global__ void __launch_bounds__(kCgThreads) cg_update_kernel(double2* __restri
                                                                const double2* __restrict__ Ap, long long M,
                                                                CgState* st, double* partials) {
   __shared__ double red[32];
+  grid_dependency_wait();
   if (st->done) return;
   const double alpha = st->alpha;
   double s = 0.0;
@@ -139,8 +142,7 @@ cudaError_t launch_cg_init(const double2* b, double2* x, double2* r, double2* p,
 
 cudaError_t launch_cg_update(double2* x, double2* r, const double2* p, const double2* Ap, long long M, CgState* st,
                              double* partials, cudaStream_t s) {
-  cg_update_kernel<<<cg_blocks(M), kCgThreads, 0, s>>>(x, r, p, Ap, M, st, partials);
-  return cudaGetLastError();
+  return launch_pdl(cg_update_kernel, dim3(cg_blocks(M)), dim3(kCgThreads), 0, s, x, r, p, Ap, M, st, partials);
 }
 
 cudaError_t launch_residual_norm(const double2* b, const double2* Ax, long long M, double* out_sum, double* partials,

@@ -129,6 +129,13 @@ template <typename TC> struct GridPos<TC, double> {
   }
 };
 
+// ---------------------------------------------------------------- launch order
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor is still running; it must
+// wait here before touching anything the predecessor writes.  Without the
+// launch attribute this returns at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------- reductions
 // Sum of v over the block (blockDim.x a multiple of 32, <= 1024).  Result
 // valid in thread 0.  Uses 32 doubles of shared scratch.

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(256) line_fft_kernel(LineGeom g, const void* _
                                                        CgArgs cga) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
+  grid_dependency_wait();
   if (INM == IN_CG || OUTM == OUT_CG) {
     if (cga.check_done && cga.st->done) return;
   }
@@ -72,8 +73,7 @@ static cudaError_t launch_one(const LineGeom& g, const void* in, void* out, int 
   const long long nlines = g.outer * g.inner;
   const long long blocks = (nlines + g.nb - 1) / g.nb;
   const size_t smem = line_fft_smem_bytes(g.L, g.nb, sizeof(cplx<T>));
-  kern<<<(unsigned)blocks, threads, smem, s>>>(g, in, out, dir, tw, what, cga);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3((unsigned)blocks), dim3(threads), smem, s, g, in, out, dir, tw, what, cga);
 }
 
 // Opt every instantiation in to the large dynamic shared-memory carve-out

@@ -61,6 +61,24 @@ cudaError_t launch_cg_persistent(const PersistentProblem* d_probs, int nprob, in
                                  cudaStream_t s);
 int persistent_cluster_size(int f64, size_t smem);
 
+// Launch `kern` with programmatic stream serialisation (the next kernel in the
+// stream may be scheduled before this one finishes; kernels that are launched
+// this way call grid_dependency_wait() first).
+template <typename K, typename... Args>
+cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ---- CG vector kernels (cg.cu)
 cudaError_t launch_cg_init(const double2* b, double2* x, double2* r, double2* p, long long M, double rho,
                            long long max_iter, CgState* st, double* partials, cudaStream_t s);
