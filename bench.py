@@ -221,6 +221,71 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU leg
+def run_batch(args, rank, world):
+    """The heterogeneous batch: 64 independent 2D Matern problems of uneven
+    size set up, CG-solved together (one persistent launch with a cluster per
+    problem, or graph branches) and evaluated at 1e4 targets each."""
+    import torch
+    import paper_2210_10210_gb300 as E
+    from paper_2210_10210_gb300 import build
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    probs = synthdata.batch_problems(seed=6 + 1000 * rank, count=args.batch_count)
+    items, targets, npts = [], [], 0
+    for rec, model in probs:
+        fam, nu, ell, sigma, eps = model
+        x, y = synthdata.make_torch(rec, dev)
+        items.append(dict(x=x, y=y, kernel=E.Kernel(fam, nu, ell), sigma=sigma, eps=eps))
+        targets.append(torch.from_numpy(synthdata.targets_np(rec)).to(dev))
+        npts += rec.n
+    torch.cuda.synchronize()
+
+    def step():
+        B = E.batch_setup(items, cg_mode=args.cg_mode)
+        infos = B.solve()
+        for i in range(len(items)):
+            B.predict(i, targets[i])
+        iters = [i["iters"] for i in infos]
+        B.close()
+        return iters, infos[0]["solve_ms"]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        solve_ms = []
+        for _ in range(args.steps):
+            iters, sms = step()
+            solve_ms.append(sms)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dev) / args.steps
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": job_throughput(npts, world, ms), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batch of {len(items)} 2D Matern-1/2 and 3/2 problems, N log-uniform "
+                                   f"[1e4, 1e7] (total {npts}), l U[0.03, 0.3], sigma U[0.1, 1], eps 1e-4, "
+                                   "1e4 iid targets each", "problems": len(items), "points": npts},
+            "cg_iters_max": max(iters), "cg_iters_median": sorted(iters)[len(iters) // 2],
+            "cg_iters_total": sum(iters), "cg_ms": sum(solve_ms) / len(solve_ms), "cg_mode": args.cg_mode,
+            "clocks": clk.summary(),
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2210_10210_gb300 as E
@@ -254,7 +319,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
 
     def step(profile=0):
-        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile)
+        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile, cg_mode=args.cg_mode)
         info = h.solve()
         mu = h.predict(z)
         pt = h.phase_times()
@@ -324,6 +389,29 @@ def run_ours(args, rank, world):
                 "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                 "peak_source": src, "alg_bytes_per_launch": alg[roof_kernel], "ms_per_launch": kt}
 
+    # posterior mean at all N training points (type-2 with q = N)
+    at_data = None
+    if args.at_data:
+        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=1)
+        h.solve()
+        mu_all = torch.empty(rec.n, dtype=y.dtype, device=dev)
+        h.predict(x, out=mu_all)
+        torch.cuda.synchronize()
+        t0 = h.phase_times()
+        reps = 3
+        for _ in range(reps):
+            h.predict(x, out=mu_all)
+        torch.cuda.synchronize()
+        t1 = h.phase_times()
+        h.close()
+        ims = (t1["interp_ms"] - t0["interp_ms"]) / reps
+        fms = (t1["predict_fft_ms"] - t0["predict_fft_ms"]) / reps
+        ib = rec.n * (d * coord_b + val_b)
+        at_data = {"points": rec.n, "interp_ms": ims, "grid_ms": fms,
+                   "interp_gbs": ib / (ims / 1000) / 1e9, "interp_frac_hbm": ib / (ims / 1000) / 1e9 / hbm,
+                   "alg_bytes": ib}
+        del mu_all
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -378,6 +466,8 @@ def run_ours(args, rank, world):
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu,
         }
+        if at_data:
+            line["mean_at_data"] = at_data
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -394,6 +484,11 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--once", action="store_true", help="run one untimed step and exit (profiling target)")
+    ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="CG launch form (0 chooses; see efgp_options.cg_mode)")
+    ap.add_argument("--at-data", action="store_true",
+                    help="also time the posterior mean at all N training points (type-2 with q = N)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "traffic.json"))
     args = ap.parse_args()
@@ -401,6 +496,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "batch":
+        run_batch(args, rank, world)
     else:
         run_ours(args, rank, world)
 

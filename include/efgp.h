@@ -85,8 +85,12 @@ typedef struct {
   int iters_per_launch; /* CG iterations per captured CUDA graph launch (0: 32)           */
   int autotune;         /* 1: time candidate FFT line batches once per shape              */
   int profile;          /* 1: time each phase with CUDA events (efgp_get_phase_times)     */
-  int cg_mode;          /* 0: choose; 1: graph-captured kernels per iteration; 2: one   */
-                        /* persistent launch on a thread-block cluster (small problems)    */
+  int cg_mode;          /* 0: choose (one problem: 1; a batch: 3);                      */
+                        /* 1: graph-captured kernels per iteration;                        */
+                        /* 2: one persistent launch, a thread-block cluster per problem     */
+                        /*    (small problems);                                            */
+                        /* 3: one launch whose blocks claim work items (FFT line batches,   */
+                        /*    vector chunks) of any problem's current CG phase             */
   void* stream;         /* cudaStream_t to order work on (NULL: a private stream)         */
 } efgp_options;
 
@@ -200,6 +204,14 @@ int efgp_get_phase_times(const efgp_handle* h, efgp_phase_times* out);
 
 /* Copy beta (M complex float64, interleaved) to host memory. */
 int efgp_get_beta(const efgp_handle* h, double* beta_host);
+
+/* Replace beta by caller-supplied weights (M complex float64, host memory,
+ * same order as efgp_get_beta); efgp_predict then evaluates
+ * f(z) = Re sum_j D_j beta_j exp(2 pi i h j.z).  With beta iid standard
+ * complex normal and beta_{-j} = conj(beta_j) this draws a sample of the GP
+ * prior with covariance ktilde (eq. 110), as suggested in Sec. 6; the random
+ * numbers are the caller's.  Marks the handle solved.  N may be 0 at set-up. */
+int efgp_set_beta(efgp_handle* h, const double* beta_host);
 
 /* Copy the Toeplitz vector w ((4m+1)^d complex) and/or the right-hand side
  * b = D F^* y (M complex) to host memory; either pointer may be NULL. */

@@ -112,6 +112,19 @@ def plan(d: int, n: int, kernel: Kernel, sigma: float, eps: float, precision="mi
     return p.as_dict()
 
 
+def prior_weights(M: int, rng) -> np.ndarray:
+    """Weights beta on J_m (row-major, M = (2m+1)^d) with E[beta_j conj(beta_k)]
+    = delta_jk and beta_{-j} = conj(beta_j), so that
+    f(z) = sum_j D_j beta_j exp(2 pi i h j.z) is real with covariance
+    sum_j D_j^2 exp(2 pi i h j.(z - z')) = ktilde(z - z') (eq. 110): a GP prior
+    draw in the Fourier basis (Sec. 6).  Drawn on the host from the numpy
+    Generator rng; the index of -j is M-1-j."""
+    z = (rng.standard_normal(M) + 1j * rng.standard_normal(M)) / np.sqrt(2.0)
+    beta = (z + np.conj(z[::-1])) / np.sqrt(2.0)
+    beta[M // 2] = rng.standard_normal()        # j = 0: real, unit variance
+    return beta
+
+
 class Handle:
     """A set-up problem (owns device workspace until closed)."""
 
@@ -182,6 +195,17 @@ class Handle:
         buf = np.empty(2 * p["M"], dtype=np.float64)
         _check(_capi.lib().efgp_get_beta(self._p, buf.ctypes.data), "efgp_get_beta")
         return buf.view(np.complex128)
+
+    def set_beta(self, beta):
+        """Use caller-supplied weights (M complex) for predict (e.g. prior samples)."""
+        b = np.ascontiguousarray(beta, dtype=np.complex128)
+        _check(_capi.lib().efgp_set_beta(self._p, b.ctypes.data), "efgp_set_beta")
+
+    def sample_prior(self, targets, rng):
+        """One draw of the GP prior (covariance ktilde, eq. 110) at targets:
+        weights from prior_weights(M, rng), then the type-2 sum."""
+        self.set_beta(prior_weights(self.params()["M"], rng))
+        return self.predict(targets)
 
     def system(self):
         """(w on J_{2m} as a (4m+1)^d complex array, b on J_m as an M vector)."""

@@ -64,12 +64,17 @@ int choose_nb(int L, long long inner, long long nlines, size_t elem) {
   int nb;
   if (inner > 1) nb = elem == 8 ? 8 : 4;
   else nb = std::max(1, std::min(16, 2048 / std::max(L, 1)));
-  const size_t cap = kLineFftMaxSmem;
+  // at most ~100 KB per block, so that two blocks share an SM
+  const size_t cap = kLineFftBlockSmem;
   while (nb > 1 && line_fft_smem_bytes(L, nb, elem) > cap) nb /= 2;
   // keep at least ~2 blocks per SM-sized wave when lines are scarce
   while (nb > 1 && (nlines + nb - 1) / nb < 304) nb /= 2;
   return nb;
 }
+
+// Threads of a line block: long batches get 512 so that an SM still holds
+// 32 warps when shared memory admits only two blocks.
+int line_threads(int L, int nb) { return (long long)L * nb >= 4096 ? 512 : 256; }
 
 void set_radices(LineGeom& g) {
   g.npass = factor_radices(g.L, g.radix);
@@ -96,7 +101,7 @@ std::vector<Pass> grid_fft_passes(int d, int n, int dir, size_t elem) {
     p.inm = IN_PLAIN;
     p.outm = OUT_PLAIN;
     p.conv = false;
-    p.threads = 256;
+    p.threads = line_threads(n, g.nb);
     ps.push_back(p);
   }
   return ps;
@@ -132,7 +137,7 @@ std::vector<Pass> matvec_passes(int d, int n1, int L, size_t elem, long long* sc
     p.inm = inm;
     p.outm = outm;
     p.conv = conv;
-    p.threads = 256;
+    p.threads = line_threads(L, g.nb);
     ps.push_back(p);
   };
   const long long n = n1, LL = L;
@@ -656,7 +661,7 @@ int persistent_prepare(efgp_handle* H, double rho, long long max_iter, bool batc
   if (H->pcluster < 0) {
     const long long grid = ipow(H->par.L, H->d);
     const int mode = H->opt.cg_mode;
-    if (mode == 1 || (mode == 0 && (grid > kPersistentMaxGrid || !batch)) || (int)H->mv.size() > kMaxPasses) {
+    if (mode != 2 || (grid > kPersistentMaxGrid && batch) || (int)H->mv.size() > kMaxPasses) {
       H->pcluster = 0;
       return EFGP_OK;
     }
@@ -716,6 +721,121 @@ int persistent_prepare(efgp_handle* H, double rho, long long max_iter, bool batc
   P.rho = rho;
   P.max_iter = max_iter;
   EFGP_CK(cudaMemcpyAsync(H->d_pprob, &P, sizeof(PersistentProblem), cudaMemcpyHostToDevice, H->stream));
+  return EFGP_OK;
+}
+
+// Dynamically scheduled CG (one launch for one or many problems): line
+// batches re-chosen so that one block's shared memory stays modest and a
+// problem alone still offers items to every resident block.
+constexpr size_t kQueueSmemCap = 100 * 1024;
+
+int queue_prepare(efgp_handle* H, double rho, long long max_iter, int resident, QueueProblem* out, size_t* smem) {
+  if ((int)H->mv.size() > kMaxPasses) {
+    set_error("too many passes for the scheduled CG kernel");
+    return EFGP_EUNSUPPORTED;
+  }
+  QueueProblem Q{};
+  PersistentProblem& P = Q.P;
+  P.npass = (int)H->mv.size();
+  const long long vec_items = (H->M + kQueueChunk - 1) / kQueueChunk;
+  long long maxitems = vec_items;
+  size_t sm = 0;
+  for (int q = 0; q < P.npass; ++q) {
+    const Pass& ps = H->mv[q];
+    LineGeom g = ps.g;
+    const long long lines = g.outer * g.inner;
+    // ~4096 elements per item (eight per thread), fewer where lines are scarce
+    int nb = std::max(1, std::min(16, 4096 / std::max(g.L, 1)));
+    while (nb > 1 && line_fft_smem_bytes(g.L, nb, H->elem) > kQueueSmemCap) nb /= 2;
+    while (nb > 1 && (lines + nb - 1) / nb < resident / 4) nb /= 2;
+    if (line_fft_smem_bytes(g.L, nb, H->elem) > (size_t)kLineFftMaxSmem) {
+      set_error("FFT length too large for the scheduled CG kernel");
+      return EFGP_EUNSUPPORTED;
+    }
+    g.nb = nb;
+    sm = std::max(sm, line_fft_smem_bytes(g.L, nb, H->elem));
+    const long long items = (lines + nb - 1) / nb;
+    Q.items[q + 1] = (int)items;
+    maxitems = std::max(maxitems, items);
+    P.pass[q] = g;
+    P.inb[q] = ps.in_buf;
+    P.outb[q] = ps.out_buf;
+    P.dir[q] = ps.dir;
+    P.inm[q] = ps.inm;
+    P.outm[q] = ps.outm;
+    P.conv[q] = ps.conv ? 1 : 0;
+  }
+  Q.items[0] = Q.items[P.npass + 1] = (int)vec_items;
+  P.buf[0] = nullptr;
+  P.buf[1] = H->scrA;
+  P.buf[2] = H->scrB;
+  P.tw = H->twL;
+  P.what = H->what;
+  P.x = H->x;
+  P.r = H->r;
+  P.p = H->p;
+  P.Ap = H->Ap;
+  P.b = H->b;
+  P.Dw = H->Dw;
+  P.sigma2 = H->sigma * H->sigma;
+  P.M = H->M;
+  P.st = H->st;
+  P.rho = rho;
+  P.max_iter = max_iter;
+  if (H->qpartials_n < maxitems) {
+    EFGP_TRY(H->alloc((void**)&H->qpartials, sizeof(double) * maxitems));
+    H->qpartials_n = maxitems;
+  }
+  if (!H->qctl) EFGP_TRY(H->alloc((void**)&H->qctl, sizeof(QueueCtl)));
+  Q.partials = H->qpartials;
+  Q.ctl = H->qctl;
+  *out = Q;
+  *smem = std::max(*smem, sm);
+  return EFGP_OK;
+}
+
+int resident_queue_blocks(int f64) {
+  // the item split is chosen for the block count at the largest line batch
+  return std::max(1, cg_queue_blocks(f64, kQueueSmemCap));
+}
+
+// One launch of the scheduled CG kernel over problems hs (descriptors qs
+// already prepared) on stream s; d_probs holds room for them and aux for two
+// counters.  Fills each problem's host CgState; returns the kernel time in ms.
+int run_queue(const std::vector<efgp_handle*>& hs, const std::vector<QueueProblem>& qs, size_t smem,
+              QueueProblem* d_probs, unsigned int* aux, CgState* host_states, cudaStream_t s, float* ms_out) {
+  const int n = (int)hs.size();
+  const int f64 = hs[0]->f64;
+  const int blocks = cg_queue_blocks(f64, smem);
+  if (blocks <= 0) {
+    set_error("scheduled CG kernel does not fit on the device");
+    return EFGP_EUNSUPPORTED;
+  }
+  for (int i = 0; i < n; ++i) EFGP_CK(cudaMemsetAsync(qs[i].ctl, 0, sizeof(QueueCtl), s));
+  EFGP_CK(cudaMemsetAsync(aux, 0, 2 * sizeof(unsigned int), s));
+  EFGP_CK(cudaMemcpyAsync(d_probs, qs.data(), sizeof(QueueProblem) * n, cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0, e1;
+  EFGP_CK(cudaEventCreate(&e0));
+  EFGP_CK(cudaEventCreate(&e1));
+  EFGP_CK(cudaEventRecord(e0, s));
+  EFGP_CK(launch_cg_queue(d_probs, n, aux, f64, smem, blocks, s));
+  EFGP_CK(cudaEventRecord(e1, s));
+  for (int i = 0; i < n; ++i)
+    EFGP_CK(cudaMemcpyAsync(&host_states[i], hs[i]->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  unsigned int haux[2] = {0, 0};
+  EFGP_CK(cudaMemcpyAsync(haux, aux, sizeof(haux), cudaMemcpyDeviceToHost, s));
+  EFGP_CK(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms;
+  for (efgp_handle* H : hs) H->times.launches += 1;
+  if (haux[1] != 0 || haux[0] != (unsigned)n) {
+    set_error("scheduled CG kernel gave up waiting for work (flags " + std::to_string(haux[1]) + ", " +
+              std::to_string(haux[0]) + " of " + std::to_string(n) + " problems finished)");
+    return EFGP_ETIMEOUT;
+  }
   return EFGP_OK;
 }
 
@@ -920,14 +1040,28 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   if (!H) return EFGP_EINVAL;
   const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
   const long long max_iter = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
-  EFGP_TRY(persistent_prepare(H, rho, max_iter, false));
-  const bool persistent = H->pcluster > 0;
-  if (!persistent) EFGP_TRY(capture_cg_graph(H));
+  const bool queued = H->opt.cg_mode == 3;
+  bool persistent = false;
+  if (!queued) {
+    EFGP_TRY(persistent_prepare(H, rho, max_iter, false));
+    persistent = H->pcluster > 0;
+    if (!persistent) EFGP_TRY(capture_cg_graph(H));
+  }
+  float qms = 0.f;
+  if (queued) {
+    std::vector<QueueProblem> qs(1);
+    size_t smem = 0;
+    EFGP_TRY(queue_prepare(H, rho, max_iter, resident_queue_blocks(H->f64), &qs[0], &smem));
+    if (!H->d_qprob) EFGP_TRY(H->alloc((void**)&H->d_qprob, sizeof(QueueProblem)));
+    if (!H->qaux) EFGP_TRY(H->alloc((void**)&H->qaux, 4 * sizeof(unsigned int)));
+    EFGP_TRY(run_queue({H}, qs, smem, H->d_qprob, H->qaux, H->host_state, H->stream, &qms));
+  }
   cudaEvent_t e0, e1;
   EFGP_CK(cudaEventCreate(&e0));
   EFGP_CK(cudaEventCreate(&e1));
   EFGP_CK(cudaEventRecord(e0, H->stream));
-  if (persistent) {
+  if (queued) {
+  } else if (persistent) {
     EFGP_CK(launch_cg_persistent(H->d_pprob, 1, H->pcluster, H->psmem, H->f64, H->stream));
     H->times.launches += 1;
     EFGP_CK(cudaMemcpyAsync(H->host_state, H->st, sizeof(CgState), cudaMemcpyDeviceToHost, H->stream));
@@ -961,6 +1095,7 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   EFGP_CK(cudaMemcpy(&tr, H->dsum, sizeof(double), cudaMemcpyDeviceToHost));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
+  if (queued) ms = qms;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   H->solved = true;
@@ -1079,6 +1214,14 @@ int efgp_get_beta(const efgp_handle* H, double* beta_host) {
   return EFGP_OK;
 }
 
+int efgp_set_beta(efgp_handle* H, const double* beta_host) {
+  if (!H || !beta_host) return EFGP_EINVAL;
+  EFGP_CK(cudaMemcpyAsync(H->x, beta_host, sizeof(double2) * H->M, cudaMemcpyHostToDevice, H->stream));
+  EFGP_CK(cudaStreamSynchronize(H->stream));
+  H->solved = true;
+  return EFGP_OK;
+}
+
 int efgp_get_system(const efgp_handle* H, double* w_host, double* b_host) {
   if (!H) return EFGP_EINVAL;
   EFGP_CK(cudaStreamSynchronize(H->stream));
@@ -1118,6 +1261,8 @@ int efgp_apply_system(efgp_handle* H, const double* in_host, double* out_host) {
 struct efgp_batch {
   std::vector<efgp_handle*> hs;
   PersistentProblem* d_probs = nullptr;   // persistent descriptors of all problems
+  QueueProblem* d_qprobs = nullptr;       // scheduled-CG descriptors of all problems
+  unsigned int* d_qaux = nullptr;
   std::vector<PersistentProblem> h_probs;
   cudaStream_t main = nullptr;
   std::vector<cudaStream_t> side;
@@ -1182,8 +1327,51 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
   if (!B) return EFGP_EINVAL;
   const int n = (int)B->hs.size();
   for (efgp_handle* h : B->hs) EFGP_CK(cudaStreamSynchronize(h->stream));
+  const int mode = B->hs[0]->opt.cg_mode;
+  // default: one launch of the scheduled CG kernel over all problems
+  if (mode == 0 || mode == 3) {
+    bool same = true;
+    for (efgp_handle* H : B->hs) same = same && H->f64 == B->hs[0]->f64;
+    if (same) {
+      std::vector<QueueProblem> qs(n);
+      size_t smem = 0;
+      const int resident = resident_queue_blocks(B->hs[0]->f64);
+      for (int i = 0; i < n; ++i) {
+        efgp_handle* H = B->hs[i];
+        const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
+        const long long mi = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
+        EFGP_TRY(queue_prepare(H, rho, mi, resident, &qs[i], &smem));
+        EFGP_CK(cudaStreamSynchronize(H->stream));
+      }
+      if (!B->d_qprobs) {
+        if (cudaMalloc((void**)&B->d_qprobs, sizeof(QueueProblem) * n) != cudaSuccess ||
+            cudaMalloc((void**)&B->d_qaux, 4 * sizeof(unsigned int)) != cudaSuccess) {
+          cudaGetLastError();
+          set_error("cudaMalloc of the batch descriptors failed");
+          return EFGP_ENOMEM;
+        }
+      }
+      float ms = 0.f;
+      EFGP_TRY(run_queue(B->hs, qs, smem, B->d_qprobs, B->d_qaux, B->host_states, B->main, &ms));
+      int rc = EFGP_OK;
+      for (int i = 0; i < n; ++i) {
+        efgp_handle* H = B->hs[i];
+        H->solved = true;
+        const CgState& st = B->host_states[i];
+        if (info) {
+          info[i].iters = st.iter;
+          info[i].rel_residual = st.bnorm2 > 0 ? std::sqrt(st.rr / st.bnorm2) : 0.0;
+          info[i].true_rel_residual = -1.0;
+          info[i].converged = st.done == 1;
+          info[i].solve_ms = ms;
+        }
+        if (st.done != 1 && rc == EFGP_OK) rc = st.done == 3 ? EFGP_ECUDA : EFGP_ENOTCONV;
+      }
+      return rc;
+    }
+  }
   // every problem small enough: one persistent launch, one cluster per problem
-  {
+  if (mode == 2) {
     bool all = true;
     int cl = 16, f64 = B->hs[0]->f64;
     size_t smem = 0;
@@ -1352,6 +1540,8 @@ void efgp_batch_destroy(efgp_batch* B) {
   if (B->main) cudaStreamSynchronize(B->main);
   for (efgp_handle* h : B->hs) efgp_destroy(h);
   if (B->d_probs) cudaFree(B->d_probs);
+  if (B->d_qprobs) cudaFree(B->d_qprobs);
+  if (B->d_qaux) cudaFree(B->d_qaux);
   if (B->graph) cudaGraphExecDestroy(B->graph);
   for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
   for (cudaStream_t s : B->side) cudaStreamDestroy(s);

@@ -24,25 +24,6 @@ namespace cg = cooperative_groups;
 namespace efgp {
 
 template <typename T>
-__device__ __forceinline__ double run_pass(const PersistentProblem& P, int q, long long blk, const CgArgs& cga,
-                                           double beta, unsigned char* smem) {
-  const LineGeom& g = P.pass[q];
-  const void* in = P.buf[P.inb[q]];
-  void* out = P.buf[P.outb[q]];
-  const cplx<T>* tw = reinterpret_cast<const cplx<T>*>(P.tw);
-  const T* what = reinterpret_cast<const T*>(P.what);
-  const int dir = P.dir[q];
-  const int inm = P.inm[q], outm = P.outm[q];
-  if (P.conv[q]) {
-    if (inm == IN_CG) return line_block<T, IN_CG, OUT_CG, true>(g, blk, in, out, dir, tw, what, cga, beta, smem);
-    return line_block<T, IN_PLAIN, OUT_PLAIN, true>(g, blk, in, out, dir, tw, what, cga, beta, smem);
-  }
-  if (inm == IN_CG) return line_block<T, IN_CG, OUT_PLAIN, false>(g, blk, in, out, dir, tw, what, cga, beta, smem);
-  if (outm == OUT_CG) return line_block<T, IN_PLAIN, OUT_CG, false>(g, blk, in, out, dir, tw, what, cga, beta, smem);
-  return line_block<T, IN_PLAIN, OUT_PLAIN, false>(g, blk, in, out, dir, tw, what, cga, beta, smem);
-}
-
-template <typename T>
 __global__ void __launch_bounds__(kPersistentThreads) cg_cluster_kernel(const PersistentProblem* __restrict__ probs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];

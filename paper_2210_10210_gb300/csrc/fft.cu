@@ -24,7 +24,7 @@
 namespace efgp {
 
 template <typename T, int INM, int OUTM, bool CONV>
-__global__ void __launch_bounds__(256) line_fft_kernel(LineGeom g, const void* __restrict__ in_v, void* out_v, int dir,
+__global__ void __launch_bounds__(kLineFftMaxThreads) line_fft_kernel(LineGeom g, const void* __restrict__ in_v, void* out_v, int dir,
                                                        const cplx<T>* __restrict__ tw, const T* __restrict__ what,
                                                        CgArgs cga) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -83,6 +83,12 @@ struct efgp_handle {
   size_t psmem = 0;
   efgp::PersistentProblem pprob{};
   efgp::PersistentProblem* d_pprob = nullptr;
+  // dynamically scheduled CG (cg_queue.cu)
+  double* qpartials = nullptr;
+  long long qpartials_n = 0;
+  efgp::QueueCtl* qctl = nullptr;
+  efgp::QueueProblem* d_qprob = nullptr;
+  unsigned int* qaux = nullptr;
   cudaEvent_t ev[8] = {};
   bool ev_made = false;
 

@@ -35,6 +35,8 @@ cudaError_t launch_line_fft(const LineGeom& g, const void* in, void* out, int di
 
 size_t line_fft_smem_bytes(int L, int nb, size_t elem_bytes);
 constexpr int kLineFftMaxSmem = 200 * 1024;   // dynamic shared memory cap of one pass
+constexpr size_t kLineFftBlockSmem = 100 * 1024;   // preferred cap (two blocks per SM)
+constexpr int kLineFftMaxThreads = 512;
 template <typename T>
 cudaError_t prepare_line_fft();
 
@@ -60,6 +62,28 @@ struct PersistentProblem {
 cudaError_t launch_cg_persistent(const PersistentProblem* d_probs, int nprob, int cluster, size_t smem, int f64,
                                  cudaStream_t s);
 int persistent_cluster_size(int f64, size_t smem);
+
+// ---- dynamically scheduled CG over many problems in one launch (cg_queue.cu)
+constexpr int kQueueThreads = 512;
+constexpr int kQueueChunk = 2048;   // vector elements per item of the init and update phases
+// Control block of one problem, in global memory, one cache line each.
+struct alignas(128) QueueCtl {
+  unsigned long long word;   // (phase sequence number << 32) | items claimed in it
+  unsigned int completed;    // items of the current phase finished
+  int done;                  // 0 running, 1 converged, 2 iteration cap, 3 breakdown
+  double rr, alpha, beta, bnorm2, tol2, pAp;
+  long long it;
+};
+struct QueueProblem {
+  PersistentProblem P;           // passes (line batches chosen for this kernel), buffers, scalars
+  int items[kMaxPasses + 2];     // work items of phase 0 (init), 1..npass (passes), npass+1 (update)
+  double* partials;              // one partial sum per item of the largest phase
+  QueueCtl* ctl;
+};
+// aux[0]: problems finished, aux[1]: error flags (host zeroes both and every ctl)
+cudaError_t launch_cg_queue(const QueueProblem* d_probs, int nprob, unsigned int* aux, int f64, size_t smem,
+                            int blocks, cudaStream_t s);
+int cg_queue_blocks(int f64, size_t smem);   // resident blocks of the kernel on the device (0: does not fit)
 
 // Launch `kern` with programmatic stream serialisation (the next kernel in the
 // stream may be scheduled before this one finishes; kernels that are launched

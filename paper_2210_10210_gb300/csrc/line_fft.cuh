@@ -1,5 +1,7 @@
 // Device functions of the batched Stockham line FFT (see fft.cu), shared
-// by the per-pass kernels and the persistent CG kernel.
+// by the per-pass kernels and the two single-launch CG kernels.  Inputs that
+// another block of the same launch may have written are read with L2-only
+// loads (__ldcg), so that no stale L1 line is ever used.
 #pragma once
 
 #include "kernels.h"
@@ -192,12 +194,12 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
     if (line < nlines && k < g.n_in) {
       const long long o = line / g.inner, i = line - o * g.inner;
       if (INM == IN_PLAIN) {
-        v = reinterpret_cast<const cplx<T>*>(in_v)[o * g.in_so + (long long)k * g.in_sk + i * g.in_si];
+        v = __ldcg(reinterpret_cast<const cplx<T>*>(in_v) + (o * g.in_so + (long long)k * g.in_sk + i * g.in_si));
       } else {
         const long long j = o * g.n_in + k;   // flat index into the M-vector
-        double2 pv = cga.src[j];
+        double2 pv = __ldcg(cga.src + j);
         if (cga.update_p) {
-          const double2 rv = cga.r[j];
+          const double2 rv = __ldcg(cga.r + j);
           pv.x = rv.x + cg_beta * pv.x;
           pv.y = rv.y + cg_beta * pv.y;
           cga.src[j] = pv;
@@ -246,7 +248,7 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
     } else {
       const long long j = o * g.n_out + k;
       const double dj = cga.Dw[j];
-      const double2 sv = cga.src[j];
+      const double2 sv = __ldcg(cga.src + j);
       double2 a;
       a.x = dj * (double)v.x + cga.sigma2 * sv.x;
       a.y = dj * (double)v.y + cga.sigma2 * sv.y;
@@ -257,6 +259,27 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
 
   __syncthreads();
   return dot;
+}
+
+// Line block blk of pass q of a problem descriptor (the CG variants of the
+// product: prologue on the first pass, epilogue on the last).
+template <typename T>
+__device__ __forceinline__ double run_pass(const PersistentProblem& P, int q, long long blk, const CgArgs& cga,
+                                           double beta, unsigned char* smem) {
+  const LineGeom& g = P.pass[q];
+  const void* in = P.buf[P.inb[q]];
+  void* out = P.buf[P.outb[q]];
+  const cplx<T>* tw = reinterpret_cast<const cplx<T>*>(P.tw);
+  const T* what = reinterpret_cast<const T*>(P.what);
+  const int dir = P.dir[q];
+  const int inm = P.inm[q], outm = P.outm[q];
+  if (P.conv[q]) {
+    if (inm == IN_CG) return line_block<T, IN_CG, OUT_CG, true>(g, blk, in, out, dir, tw, what, cga, beta, smem);
+    return line_block<T, IN_PLAIN, OUT_PLAIN, true>(g, blk, in, out, dir, tw, what, cga, beta, smem);
+  }
+  if (inm == IN_CG) return line_block<T, IN_CG, OUT_PLAIN, false>(g, blk, in, out, dir, tw, what, cga, beta, smem);
+  if (outm == OUT_CG) return line_block<T, IN_PLAIN, OUT_CG, false>(g, blk, in, out, dir, tw, what, cga, beta, smem);
+  return line_block<T, IN_PLAIN, OUT_PLAIN, false>(g, blk, in, out, dir, tw, what, cga, beta, smem);
 }
 
 }  // namespace efgp

@@ -146,24 +146,27 @@ def test_toeplitz_apply_matches_dense(E):
 
 @pytest.mark.parametrize("name,n,prec", [("matern2d", 100_000, "mixed"), ("se3d", 50_000, "mixed"),
                                          ("se1d", 10_000, "fp64"), ("matern2d", 20_000, "fp64")])
-def test_persistent_cluster_cg_matches_graph_cg(E, name, n, prec):
-    # one persistent launch on a thread-block cluster vs graph-captured
-    # per-pass kernels: same iterations up to rounding, same mean
+def test_single_launch_cg_matches_graph_cg(E, name, n, prec):
+    # one persistent launch on a thread-block cluster (mode 2) and one launch
+    # of the work-claiming scheduled kernel (mode 3) vs graph-captured per-pass
+    # kernels (mode 1): same iterations up to rounding, same mean
     rec = synthdata.config(name, n=n)
     x, y, z = synthdata.make_np(rec)
     z = z[:5000]
     ek, ok, sigma, eps = _kernel(E, synthdata.MODELS[name])
     out = {}
-    for mode in (1, 2):
+    for mode in (1, 2, 3):
         h = E.setup(_dev(x), _dev(y), ek, sigma, eps, precision=prec, cg_mode=mode)
         info = h.solve()
         assert info["converged"], (mode, info)
         out[mode] = (info, h.predict(_dev(z)).double().cpu().numpy())
         h.close()
-    (i1, m1), (i2, m2) = out[1], out[2]
-    assert abs(i1["iters"] - i2["iters"]) <= max(3, 0.05 * i1["iters"])
-    assert np.abs(m1 - m2).max() <= 0.2 * 10 * eps * np.abs(y).max()
-    assert i2["true_rel_residual"] <= 10 * eps
+    i1, m1 = out[1]
+    for mode in (2, 3):
+        i2, m2 = out[mode]
+        assert abs(i1["iters"] - i2["iters"]) <= max(3, 0.05 * i1["iters"]), mode
+        assert np.abs(m1 - m2).max() <= 0.2 * 10 * eps * np.abs(y).max(), mode
+        assert i2["true_rel_residual"] <= 10 * eps, mode
 
 
 def test_ragged_tiny_and_edge_points(E):
@@ -289,3 +292,67 @@ def test_batch_matches_single_and_oracle(E):
         h.solve()
         mu1 = h.predict(_dev(z)).double().cpu().numpy()
         assert np.abs(mu - mu1).max() <= 0.2 * 10 * eps * np.abs(y).max(), i
+
+
+@pytest.mark.parametrize("name,n", [("matern2d", 20000), ("se3d", 0)])
+def test_prior_sample_matches_oracle_type2(E, name, n):
+    """A GP prior draw (Sec. 6): caller-supplied weights through efgp_set_beta,
+    then the type-2 sum, against the oracle's direct sum with the same weights.
+    N = 0 needs no data: the prior is drawn before any observation."""
+    rec = synthdata.config(name, n=n)
+    x, y, z = synthdata.make_np(rec)
+    z = z[:5000]
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS[name])
+    d = x.shape[1]
+    h = E.setup(_dev(x), _dev(y), ek, sigma, eps)
+    par = h.params()
+    beta = E.prior_weights(par["M"], np.random.default_rng(5))
+    h.set_beta(beta)
+    f = h.predict(_dev(z)).double().cpu().numpy()
+    f2 = h.sample_prior(_dev(z), np.random.default_rng(5)).double().cpu().numpy()
+    h.close()
+    hh, m = O.choose_h_m(ok, d, eps)
+    assert m == par["m"]
+    D = O.spectral_weights(ok, d, hh, m)
+    ref = O.mean_at(z, beta, D, hh, m)
+    assert np.abs(ref.imag).max() <= 1e-9 * np.abs(ref.real).max()
+    # type-2 NUFFT error bound: tol sum_j |D_j beta_j|
+    bound = 3 * (eps / 10) * np.abs(D * beta).sum()
+    assert np.abs(f - ref.real).max() <= bound, (np.abs(f - ref.real).max(), bound)
+    assert np.array_equal(f, f2)
+
+
+def test_scheduled_batch_with_empty_and_large_problems(E):
+    """The one-launch batched CG over problems of very different size: an
+    empty problem (finishes at initialisation), a long-lengthscale small one
+    and a short-lengthscale Matern-1/2 one whose FFT grid (L > 1000) is far
+    beyond one thread-block cluster.  Each must agree with its own
+    single-problem graph-captured solve."""
+    specs = [(0, ("matern", 1.5, 0.2, 0.5, 1e-4)), (30_000, ("matern", 1.5, 0.25, 0.4, 1e-4)),
+             (200_000, ("matern", 0.5, 0.03, 0.3, 1e-4))]
+    items, cases = [], []
+    for k, (n, model) in enumerate(specs):
+        rec = synthdata.config("matern2d", n=n)
+        rec.seed = 40 + k
+        rec.targets, rec.n_targets = "iid", 2000
+        x, y, z = synthdata.make_np(rec)
+        ek, ok, sigma, eps = _kernel(E, model)
+        items.append(dict(x=_dev(x), y=_dev(y), kernel=ek, sigma=sigma, eps=eps))
+        cases.append((x, y, z, ek, sigma, eps))
+    B = E.batch_setup(items)
+    assert B.params(2)["L"] > 1000
+    infos = B.solve()
+    assert all(i["converged"] for i in infos), infos
+    assert infos[0]["iters"] == 0
+    for i, (x, y, z, ek, sigma, eps) in enumerate(cases):
+        mu = B.predict(i, _dev(z)).double().cpu().numpy()
+        if i == 0:
+            assert np.all(mu == 0)
+            continue
+        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, cg_mode=1)
+        i1 = h.solve()
+        mu1 = h.predict(_dev(z)).double().cpu().numpy()
+        h.close()
+        assert abs(i1["iters"] - infos[i]["iters"]) <= max(3, 0.05 * i1["iters"]), (i, i1, infos[i])
+        assert np.abs(mu - mu1).max() <= 0.2 * 10 * eps * np.abs(y).max(), i
+    B.close()
