@@ -71,6 +71,53 @@ __device__ __forceinline__ void dft_generic(cplx<T>* v, int dir) {
   for (int q = 0; q < R; ++q) v[q] = o[q];
 }
 
+// Odd R: with a_r = v_r + v_{R-r} and b_r = v_r - v_{R-r} (r = 1..(R-1)/2),
+// out[q] = v_0 + sum_r a_r cos(2 pi r q / R) + i dir sum_r b_r sin(2 pi r q / R)
+// and out[R-q] the same with the sine sum negated (the pairs' exponentials are
+// complex conjugates), about a third of the multiply-adds of the plain sum.
+template <typename T, int R>
+__device__ __forceinline__ void dft_odd(cplx<T>* v, int dir) {
+  constexpr int H = (R - 1) / 2;
+  cplx<T> a[H], b[H];
+  cplx<T> y0 = v[0];
+#pragma unroll
+  for (int r = 1; r <= H; ++r) {
+    a[r - 1] = cadd(v[r], v[R - r]);
+    b[r - 1] = csub(v[r], v[R - r]);
+    y0 = cadd(y0, a[r - 1]);
+  }
+  const T fd = (T)dir;
+  cplx<T> o[R];
+  o[0] = y0;
+#pragma unroll
+  for (int q = 1; q <= H; ++q) {
+    T ax = v[0].x, ay = v[0].y, bx = T(0), by = T(0);
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      const int k = (r * q) % R;
+      const T c = Roots<T, R>::c(k), sn = Roots<T, R>::s(k);
+      ax = fma(a[r - 1].x, c, ax);
+      ay = fma(a[r - 1].y, c, ay);
+      bx = fma(b[r - 1].x, sn, bx);
+      by = fma(b[r - 1].y, sn, by);
+    }
+    const T ix = -fd * by, iy = fd * bx;   // i dir (bx + i by)
+    o[q] = mk<T>(ax + ix, ay + iy);
+    o[R - q] = mk<T>(ax - ix, ay - iy);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = o[q];
+}
+
+// a / b for 0 <= a < 2^24, 0 < b, with rb ~ 1/b: a float estimate corrected by one step
+__device__ __forceinline__ int quick_div(int a, int b, float rb) {
+  int q = __float2int_rz(__int2float_rn(a) * rb);
+  const int r = a - q * b;
+  if (r < 0) --q;
+  else if (r >= b) ++q;
+  return q;
+}
+
 template <typename T>
 __device__ __forceinline__ void dft2(cplx<T>& a, cplx<T>& b) {
   cplx<T> t = a;
@@ -111,7 +158,7 @@ __device__ __forceinline__ void dft(cplx<T>* v, int dir) {
   if constexpr (R == 2) dft2<T>(v[0], v[1]);
   else if constexpr (R == 4) dft4<T>(v, dir);
   else if constexpr (R == 8) dft8<T>(v, dir);
-  else dft_generic<T, R>(v, dir);
+  else dft_odd<T, R>(v, dir);
 }
 
 // One radix-R Stockham pass over nb lines in shared memory.
@@ -120,24 +167,26 @@ __device__ __forceinline__ void stockham_pass(const cplx<T>* __restrict__ src, c
                                               int LP, int nb, int Ns, int dir, const cplx<T>* __restrict__ tw) {
   const int nbf = L / R;
   const int tstride = L / (Ns * R);
+  const float rnbf = 1.0f / (float)nbf, rns = 1.0f / (float)Ns;
   for (int bidx = threadIdx.x; bidx < nb * nbf; bidx += blockDim.x) {
-    const int li = bidx / nbf;
+    const int li = nb == 1 ? 0 : quick_div(bidx, nbf, rnbf);
     const int j = bidx - li * nbf;
-    const int k = j % Ns;
+    const int k = j - quick_div(j, Ns, rns) * Ns;   // j mod Ns
     const cplx<T>* s = src + li * LP;
     cplx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[j + r * nbf];
     if (Ns > 1) {
+      const int kt = k * tstride;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cplx<T> t = __ldg(tw + k * r * tstride);
+        cplx<T> t = __ldg(tw + r * kt);
         if (dir > 0) t.y = -t.y;
         v[r] = cmul(v[r], t);
       }
     }
     dft<T, R>(v, dir);
-    cplx<T>* d = dst + li * LP + (j / Ns) * Ns * R + k;
+    cplx<T>* d = dst + li * LP + (j - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[r * Ns] = v[r];
   }

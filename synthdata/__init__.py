@@ -272,6 +272,9 @@ def config(name: str, n: int | None = None) -> Recipe:
     elif name == "matern2d_table4":  # the paper's Table 4 shape: l=0.1, sigma=0.1, eps=1e-5
         r = Recipe(d=2, n=1_000_000_000, seed=5, noise=0.1, fn="plane", omega=(3.0, 4.0),
                    targets="grid", n_targets_1d=1000)
+    elif name == "matern2d_table5":  # Table 5 regime: N / sigma^2 = 3e8 fixed, sigma = 1.83 at N = 1e9
+        r = Recipe(d=2, n=1_000_000_000, seed=7, noise=TABLE5_SIGMA, fn="plane", omega=(3.0, 4.0),
+                   targets="grid", n_targets_1d=1000)
     else:
         raise KeyError(name)
     if n is not None:
@@ -280,12 +283,16 @@ def config(name: str, n: int | None = None) -> Recipe:
 
 
 # GP model of each named workload: (family, nu, lengthscale, sigma, eps)
+# Sec. 5.4, Table 5: noise and regression sigma grow as sqrt(N / 3e8)
+TABLE5_SIGMA = math.sqrt(1e9 / 3e8)
+
 MODELS = {
     "se1d": ("se", 0.0, 0.1, 0.3, 1e-6),
     "matern2d": ("matern", 1.5, 0.1, 0.3, 1e-4),
     "se3d": ("se", 0.0, 0.2, 0.5, 1e-5),
     "matern2d_1e9": ("matern", 1.5, 0.05, 0.5, 1e-3),
     "matern2d_table4": ("matern", 1.5, 0.1, 0.1, 1e-5),
+    "matern2d_table5": ("matern", 1.5, 0.1, TABLE5_SIGMA, 1e-5),
 }
 
 

@@ -44,7 +44,8 @@ def _plan(family, nu, ell, d, sigma, eps, n=10_000, **kw):
     return E.plan(d, n, E.Kernel(family, nu, ell), sigma, eps, **kw)
 
 
-@pytest.mark.parametrize("name", ["se1d", "matern2d", "se3d", "matern2d_1e9", "matern2d_table4"])
+@pytest.mark.parametrize("name", ["se1d", "matern2d", "se3d", "matern2d_1e9", "matern2d_table4",
+                                  "matern2d_table5"])
 def test_host_plan_matches_oracle_h_m(capi, name):
     import synthdata
     from oracle import efgp_oracle as O
@@ -59,6 +60,16 @@ def test_host_plan_matches_oracle_h_m(capi, name):
     # the NUFFT plans meet the default tolerance eps/10
     assert p["es_err1"] <= eps / 10 and p["es_err2"] <= eps / 10
     assert p["nf1"] >= 4 * m + 1 and p["nf2"] >= 2 * m + 1
+
+
+@pytest.mark.parametrize("nu,d,ell,eps", [(3.5, 1, 0.1, 1e-6), (3.5, 2, 0.3, 1e-3), (4.5, 2, 0.1, 1e-3),
+                                          (3.5, 3, 0.4, 1e-2)])
+def test_host_plan_matches_oracle_for_matern_above_5_2(capi, nu, d, ell, eps):
+    from oracle import efgp_oracle as O
+    p = _plan("matern", nu, ell, d, 0.3, eps)
+    h, m = O.choose_h_m(O.Kernel("matern", nu, ell), d, eps)
+    assert p["m"] == m and abs(p["h"] - h) <= 1e-12
+    assert p["es_err1"] <= eps / 10 and p["es_err2"] <= eps / 10
 
 
 @pytest.mark.parametrize("row", [("matern", 0.5, 0.1, 2, 1e-3, 97), ("matern", 1.5, 0.1, 2, 1e-5, 94),

@@ -356,3 +356,25 @@ def test_scheduled_batch_with_empty_and_large_problems(E):
         assert abs(i1["iters"] - infos[i]["iters"]) <= max(3, 0.05 * i1["iters"]), (i, i1, infos[i])
         assert np.abs(mu - mu1).max() <= 0.2 * 10 * eps * np.abs(y).max(), i
     B.close()
+
+
+@pytest.mark.parametrize("model,d,n", [(("matern", 3.5, 0.3, 0.3, 1e-3), 2, 50_000),
+                                       (("matern", 4.5, 0.1, 0.3, 1e-6), 1, 50_000)])
+def test_matern_above_5_2_uniform_bound_parameters(E, model, d, n):
+    """Matern nu > 5/2 takes (h, m) from the uniform bound eq. maternhm; the
+    GPU path with those parameters against the oracle."""
+    rec = synthdata.config("matern2d" if d == 2 else "se1d", n=n)
+    rec.targets, rec.n_targets = "iid", 3000
+    x, y, z = synthdata.make_np(rec)
+    ek, ok, sigma, eps = _kernel(E, model)
+    prec = "mixed" if eps >= 1e-4 else "fp64"
+    h = E.setup(_dev(x), _dev(y), ek, sigma, eps, precision=prec)
+    info = h.solve()
+    mu = h.predict(_dev(z)).double().cpu().numpy()
+    par = h.params()
+    h.close()
+    hh, m = O.choose_h_m(ok, d, eps)
+    assert par["m"] == m and abs(par["h"] - hh) < 1e-12
+    ref = O.efgp(x, y, z, ok, sigma, eps)
+    assert info["converged"]
+    assert np.abs(mu - ref.mu).max() <= 10 * eps * np.abs(y).max()

@@ -34,7 +34,8 @@ def _numerical_khat(kern, d, xi):
                for a, b in zip(pts[:-1], pts[1:]))
 
 
-@pytest.mark.parametrize("family,nu", [("se", 0.0), ("matern", 0.5), ("matern", 1.5), ("matern", 2.5)])
+@pytest.mark.parametrize("family,nu", [("se", 0.0), ("matern", 0.5), ("matern", 1.5), ("matern", 2.5),
+                                       ("matern", 3.5)])
 @pytest.mark.parametrize("d", [1, 2, 3])
 def test_khat_is_fourier_transform_of_k(family, nu, d):
     kern = O.Kernel(family, nu, 0.1)
@@ -112,6 +113,22 @@ def test_se_choice_meets_uniform_bound(d, ell, eps):
     pts = np.stack([a.ravel() for a in np.meshgrid(*([g] * d), indexing="ij")], 1)
     err = np.abs(O.ktilde(pts, kern, h, m) - kern.k(np.sqrt((pts ** 2).sum(1))))
     assert err.max() <= eps
+
+
+@pytest.mark.parametrize("nu,d,ell,eps", [(3.5, 1, 0.1, 1e-6), (3.5, 2, 0.2, 1e-4), (4.5, 2, 0.1, 1e-3),
+                                          (3.5, 3, 0.4, 1e-2)])
+def test_matern_high_nu_choice_meets_uniform_bound(nu, d, ell, eps):
+    # Sec. 4.2, eq. maternhm: for nu > 5/2 the (h, m) choice is the one that
+    # guarantees |ktilde - k| <= eps uniformly on [-1,1]^d (the heuristic
+    # L2 choice is only for nu <= 5/2)
+    kern = O.Kernel("matern", nu, ell)
+    h, m = O.choose_h_m(kern, d, eps)
+    h2, m2 = O.choose_h_m(O.Kernel("matern", 2.5, ell), d, eps)
+    assert (h, m) != (h2, m2)
+    g = np.linspace(-1, 1, {1: 801, 2: 61, 3: 17}[d])
+    pts = np.stack([a.ravel() for a in np.meshgrid(*([g] * d), indexing="ij")], 1)
+    err = np.abs(O.ktilde(pts, kern, h, m) - kern.k(np.sqrt((pts ** 2).sum(1))))
+    assert err.max() <= eps, err.max()
 
 
 def test_pointwise_error_split_prop3():
