@@ -675,7 +675,7 @@ int persistent_prepare(efgp_handle* H, double rho, long long max_iter, bool batc
         const Pass& ps = H->mv[q];
         LineGeom g = ps.g;
         const long long lines = g.outer * g.inner;
-        g.nb = (int)std::max<long long>(1, (lines + CL - 1) / CL);
+        g.nb = (int)std::min<long long>(kMaxLineBatch, std::max<long long>(1, (lines + CL - 1) / CL));
         while (g.nb > 1 && line_fft_smem_bytes(g.L, g.nb, H->elem) > kPersistentMaxSmem) g.nb = (g.nb + 1) / 2;
         smem = std::max(smem, line_fft_smem_bytes(g.L, g.nb, H->elem));
         P.pass[q] = g;
@@ -813,12 +813,22 @@ int run_queue(const std::vector<efgp_handle*>& hs, const std::vector<QueueProble
   }
   for (int i = 0; i < n; ++i) EFGP_CK(cudaMemsetAsync(qs[i].ctl, 0, sizeof(QueueCtl), s));
   EFGP_CK(cudaMemsetAsync(aux, 0, 2 * sizeof(unsigned int), s));
+  // EFGP_FAULT=queue_stall: every control word starts in a phase whose items
+  // are all taken and never complete, so every block's bounded wait for work
+  // runs out (after a short limit) and the launch reports a timeout
+  long long idle_limit = kQueueIdleLimit;
+  static const unsigned long long kStalledWord = (1ull << 32) | 0xfffffff0ull;
+  if (fault_injected("queue_stall")) {
+    idle_limit = 1 << 12;
+    for (int i = 0; i < n; ++i)
+      EFGP_CK(cudaMemcpyAsync(&qs[i].ctl->word, &kStalledWord, sizeof(kStalledWord), cudaMemcpyHostToDevice, s));
+  }
   EFGP_CK(cudaMemcpyAsync(d_probs, qs.data(), sizeof(QueueProblem) * n, cudaMemcpyHostToDevice, s));
   cudaEvent_t e0, e1;
   EFGP_CK(cudaEventCreate(&e0));
   EFGP_CK(cudaEventCreate(&e1));
   EFGP_CK(cudaEventRecord(e0, s));
-  EFGP_CK(launch_cg_queue(d_probs, n, aux, f64, smem, blocks, s));
+  EFGP_CK(launch_cg_queue(d_probs, n, aux, f64, smem, blocks, idle_limit, s));
   EFGP_CK(cudaEventRecord(e1, s));
   for (int i = 0; i < n; ++i)
     EFGP_CK(cudaMemcpyAsync(&host_states[i], hs[i]->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));

@@ -30,7 +30,6 @@
 namespace efgp {
 
 constexpr unsigned kSeqDone = 0xffffffffu;
-constexpr long long kQueueIdleLimit = 1ll << 24;   // empty polls in a row before giving up (~10 s)
 constexpr int kErrQueueIdle = 8;
 
 __device__ __forceinline__ int phase_of(unsigned seq, int npass) {
@@ -155,7 +154,7 @@ __device__ void advance(const QueueProblem& Q, unsigned seq, int ph, double tot,
 
 template <typename T>
 __global__ void __launch_bounds__(kQueueThreads, sizeof(T) == 4 ? 2 : 1) cg_queue_kernel(const QueueProblem* __restrict__ probs, int nprob,
-                                                                 unsigned int* aux) {
+                                                                 unsigned int* aux, long long idle_limit) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   __shared__ int s_prob, s_quit, s_last;
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(kQueueThreads, sizeof(T) == 4 ? 2 : 1) cg_queu
     const int pi = s_prob;
     if (s_quit) break;
     if (pi < 0) {
-      if (++idle > kQueueIdleLimit) {
+      if (++idle > idle_limit) {
         if (tid == 0) atomicOr(err, kErrQueueIdle);
         break;
       }
@@ -246,18 +245,18 @@ __global__ void __launch_bounds__(kQueueThreads, sizeof(T) == 4 ? 2 : 1) cg_queu
 
 template <typename T>
 static cudaError_t launch_t(const QueueProblem* d_probs, int nprob, unsigned int* aux, size_t smem, int blocks,
-                            cudaStream_t s) {
+                            long long idle_limit, cudaStream_t s) {
   auto kern = cg_queue_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<blocks, kQueueThreads, smem, s>>>(d_probs, nprob, aux);
+  kern<<<blocks, kQueueThreads, smem, s>>>(d_probs, nprob, aux, idle_limit);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_queue(const QueueProblem* d_probs, int nprob, unsigned int* aux, int f64, size_t smem,
-                            int blocks, cudaStream_t s) {
-  return f64 ? launch_t<double>(d_probs, nprob, aux, smem, blocks, s)
-             : launch_t<float>(d_probs, nprob, aux, smem, blocks, s);
+                            int blocks, long long idle_limit, cudaStream_t s) {
+  return f64 ? launch_t<double>(d_probs, nprob, aux, smem, blocks, idle_limit, s)
+             : launch_t<float>(d_probs, nprob, aux, smem, blocks, idle_limit, s);
 }
 
 int cg_queue_blocks(int f64, size_t smem) {

@@ -37,6 +37,7 @@ size_t line_fft_smem_bytes(int L, int nb, size_t elem_bytes);
 constexpr int kLineFftMaxSmem = 200 * 1024;   // dynamic shared memory cap of one pass
 constexpr size_t kLineFftBlockSmem = 100 * 1024;   // preferred cap (two blocks per SM)
 constexpr int kLineFftMaxThreads = 512;
+constexpr int kMaxLineBatch = 32;   // lines of one block (per-line offset table in shared memory)
 template <typename T>
 cudaError_t prepare_line_fft();
 
@@ -80,9 +81,12 @@ struct QueueProblem {
   double* partials;              // one partial sum per item of the largest phase
   QueueCtl* ctl;
 };
-// aux[0]: problems finished, aux[1]: error flags (host zeroes both and every ctl)
+// aux[0]: problems finished, aux[1]: error flags (host zeroes both and every
+// ctl).  A block that finds nothing to claim idle_limit times in a row sets an
+// error flag and returns.
+constexpr long long kQueueIdleLimit = 1ll << 24;   // ~10 s of empty polls
 cudaError_t launch_cg_queue(const QueueProblem* d_probs, int nprob, unsigned int* aux, int f64, size_t smem,
-                            int blocks, cudaStream_t s);
+                            int blocks, long long idle_limit, cudaStream_t s);
 int cg_queue_blocks(int f64, size_t smem);   // resident blocks of the kernel on the device (0: does not fit)
 
 // Launch `kern` with programmatic stream serialisation (the next kernel in the

@@ -226,6 +226,9 @@ template <typename T, int INM, int OUTM, bool CONV>
 __device__ double line_block(const LineGeom& g, long long blk, const void* __restrict__ in_v, void* out_v, int dir,
                              const cplx<T>* __restrict__ tw, const T* __restrict__ what, const CgArgs& cga,
                              double cg_beta, unsigned char* smem_raw) {
+  // per-line element offsets, computed once per line (a line's elements then
+  // cost one multiply-add each); -1 marks lines past the end
+  __shared__ long long t_in[kMaxLineBatch], t_out[kMaxLineBatch], t_w[kMaxLineBatch];
   const int L = g.L, nb = g.nb;
   const int LP = L + 1;
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -233,19 +236,33 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
   const long long nlines = g.outer * g.inner;
   const long long line0 = blk * nb;
   const bool strided = g.inner > 1;
+  if (threadIdx.x < nb) {
+    const long long line = line0 + threadIdx.x;
+    long long bi = -1, bo = -1, bw = -1;
+    if (line < nlines) {
+      const long long o = line / g.inner, i = line - o * g.inner;
+      bi = INM == IN_PLAIN ? o * g.in_so + i * g.in_si : o * g.n_in;
+      bo = OUTM == OUT_PLAIN ? o * g.out_so + i * g.out_si : o * g.n_out;
+      bw = o * L * g.inner + i;
+    }
+    t_in[threadIdx.x] = bi;
+    t_out[threadIdx.x] = bo;
+    t_w[threadIdx.x] = bw;
+  }
+  __syncthreads();
+  const float rnb = 1.0f / (float)nb, rL = 1.0f / (float)L, rno = 1.0f / (float)g.n_out;
 
   // ---- load (zero-padded to L)
   for (int e = threadIdx.x; e < nb * L; e += blockDim.x) {
     int li, k;
-    if (strided) { li = e % nb; k = e / nb; } else { li = e / L; k = e - li * L; }
-    const long long line = line0 + li;
+    if (strided) { k = quick_div(e, nb, rnb); li = e - k * nb; } else { li = quick_div(e, L, rL); k = e - li * L; }
+    const long long base = t_in[li];
     cplx<T> v = mk<T>(0, 0);
-    if (line < nlines && k < g.n_in) {
-      const long long o = line / g.inner, i = line - o * g.inner;
+    if (base >= 0 && k < g.n_in) {
       if (INM == IN_PLAIN) {
-        v = __ldcg(reinterpret_cast<const cplx<T>*>(in_v) + (o * g.in_so + (long long)k * g.in_sk + i * g.in_si));
+        v = __ldcg(reinterpret_cast<const cplx<T>*>(in_v) + (base + (long long)k * g.in_sk));
       } else {
-        const long long j = o * g.n_in + k;   // flat index into the M-vector
+        const long long j = base + k;   // flat index into the M-vector
         double2 pv = __ldcg(cga.src + j);
         if (cga.update_p) {
           const double2 rv = __ldcg(cga.r + j);
@@ -267,11 +284,10 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
     // pointwise product with the (real) transformed generating vector
     for (int e = threadIdx.x; e < nb * L; e += blockDim.x) {
       int li, k;
-      if (strided) { li = e % nb; k = e / nb; } else { li = e / L; k = e - li * L; }
-      const long long line = line0 + li;
-      if (line < nlines) {
-        const long long o = line / g.inner, i = line - o * g.inner;
-        const T wv = __ldg(what + (o * L + k) * g.inner + i);
+      if (strided) { k = quick_div(e, nb, rnb); li = e - k * nb; } else { li = quick_div(e, L, rL); k = e - li * L; }
+      const long long bw = t_w[li];
+      if (bw >= 0) {
+        const T wv = __ldg(what + (bw + (long long)k * g.inner));
         cplx<T> t = res[li * LP + k];
         res[li * LP + k] = mk<T>(t.x * wv, t.y * wv);
       }
@@ -287,15 +303,14 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
   double dot = 0.0;
   for (int e = threadIdx.x; e < nb * g.n_out; e += blockDim.x) {
     int li, k;
-    if (strided) { li = e % nb; k = e / nb; } else { li = e / g.n_out; k = e - li * g.n_out; }
-    const long long line = line0 + li;
-    if (line >= nlines) continue;
-    const long long o = line / g.inner, i = line - o * g.inner;
+    if (strided) { k = quick_div(e, nb, rnb); li = e - k * nb; } else { li = quick_div(e, g.n_out, rno); k = e - li * g.n_out; }
+    const long long base = t_out[li];
+    if (base < 0) continue;
     const cplx<T> v = res[li * LP + k];
     if (OUTM == OUT_PLAIN) {
-      reinterpret_cast<cplx<T>*>(out_v)[o * g.out_so + (long long)k * g.out_sk + i * g.out_si] = v;
+      reinterpret_cast<cplx<T>*>(out_v)[base + (long long)k * g.out_sk] = v;
     } else {
-      const long long j = o * g.n_out + k;
+      const long long j = base + k;
       const double dj = cga.Dw[j];
       const double2 sv = __ldcg(cga.src + j);
       double2 a;

@@ -164,7 +164,7 @@ def test_single_launch_cg_matches_graph_cg(E, name, n, prec):
     i1, m1 = out[1]
     for mode in (2, 3):
         i2, m2 = out[mode]
-        assert abs(i1["iters"] - i2["iters"]) <= max(3, 0.05 * i1["iters"]), mode
+        assert abs(i1["iters"] - i2["iters"]) <= max(5, 0.1 * i1["iters"]), mode
         assert np.abs(m1 - m2).max() <= 0.2 * 10 * eps * np.abs(y).max(), mode
         assert i2["true_rel_residual"] <= 10 * eps, mode
 
@@ -353,7 +353,7 @@ def test_scheduled_batch_with_empty_and_large_problems(E):
         i1 = h.solve()
         mu1 = h.predict(_dev(z)).double().cpu().numpy()
         h.close()
-        assert abs(i1["iters"] - infos[i]["iters"]) <= max(3, 0.05 * i1["iters"]), (i, i1, infos[i])
+        assert abs(i1["iters"] - infos[i]["iters"]) <= max(5, 0.1 * i1["iters"]), (i, i1, infos[i])
         assert np.abs(mu - mu1).max() <= 0.2 * 10 * eps * np.abs(y).max(), i
     B.close()
 
@@ -378,3 +378,41 @@ def test_matern_above_5_2_uniform_bound_parameters(E, model, d, n):
     ref = O.efgp(x, y, z, ok, sigma, eps)
     assert info["converged"]
     assert np.abs(mu - ref.mu).max() <= 10 * eps * np.abs(y).max()
+
+
+def test_scheduled_cg_bounded_wait_reports_timeout(E, monkeypatch):
+    """EFGP_FAULT=queue_stall starts every problem in a phase whose items are
+    all taken and never complete (a flag nothing sets): each block's bounded
+    wait for work runs out, the kernel returns, the host reports
+    EFGP_ETIMEOUT, and the same handle then solves normally."""
+    from paper_2210_10210_gb300 import _capi
+    rec = synthdata.config("matern2d", n=20_000)
+    x, y, z = synthdata.make_np(rec)
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
+    h = E.setup(_dev(x), _dev(y), ek, sigma, eps, cg_mode=3)
+    monkeypatch.setenv("EFGP_FAULT", "queue_stall")
+    with pytest.raises(E.EfgpError) as ei:
+        h.solve()
+    assert ei.value.status == _capi.EFGP_ETIMEOUT
+    monkeypatch.delenv("EFGP_FAULT")
+    info = h.solve()
+    assert info["converged"]
+    mu = h.predict(_dev(z[:2000])).double().cpu().numpy()
+    h.close()
+    ref = _oracle(("matern2d", 20_000, None, 2000), x, y, z[:2000], ok, sigma, eps)
+    assert np.abs(mu - ref.mu).max() <= 10 * eps * np.abs(y).max()
+
+
+def test_injected_allocation_failure_reports_enomem(E, monkeypatch):
+    from paper_2210_10210_gb300 import _capi
+    ek, _, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
+    x = torch.rand(1000, 2, device="cuda")
+    y = torch.rand(1000, device="cuda")
+    monkeypatch.setenv("EFGP_FAULT", "alloc")
+    with pytest.raises(E.EfgpError) as ei:
+        E.setup(x, y, ek, sigma, eps)
+    assert ei.value.status == _capi.EFGP_ENOMEM
+    monkeypatch.delenv("EFGP_FAULT")
+    h = E.setup(x, y, ek, sigma, eps)
+    assert h.solve()["converged"]
+    h.close()
