@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(kTmaScatterThreads, 1)
     const float* sx = stage + b * SB;
     int tt[PPT];
     unsigned int rk[PPT];
+    float qk[PPT][D];   // tile-local coordinates, kept for the write-out
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int k = p * NT + tid;
@@ -404,6 +405,8 @@ __global__ void __launch_bounds__(kTmaScatterThreads, 1)
       bool bad = false;
       float q[3];
       tt[p] = tile_of_coords<D, float, float>(xa, sg, q, bad);
+#pragma unroll
+      for (int a = 0; a < D; ++a) qk[p][a] = q[a];
       rk[p] = atomicAdd(&hist[tt[p]], 1u);
     }
     __syncthreads();
@@ -424,15 +427,9 @@ __global__ void __launch_bounds__(kTmaScatterThreads, 1)
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int k = p * NT + tid;
-      float xa[3];
-#pragma unroll
-      for (int a = 0; a < D; ++a) xa[a] = sx[k * D + a];
-      bool bad = false;
-      float q[3];
-      tile_of_coords<D, float, float>(xa, sg, q, bad);
       const int pos = lstart[tt[p]] + (int)rk[p];
 #pragma unroll
-      for (int a = 0; a < D; ++a) sq[a * P + pos] = q[a];
+      for (int a = 0; a < D; ++a) sq[a * P + pos] = qk[p][a];
       sq[D * P + pos] = sx[D * P + k];
       stile[pos] = tt[p];
     }
