@@ -173,7 +173,7 @@ void fill_coef(const NufftPlan& p, EsCoef<T>* c) {
   std::memset(c, 0, sizeof(*c));
   c->deg = p.deg;
   for (int k = 0; k <= p.deg; ++k)
-    for (int j = 0; j < p.w; ++j) c->c[k * p.w + j] = (T)p.coef[(size_t)k * p.w + j];
+    for (int j = 0; j < p.w; ++j) c->c[k * es_stride(p.w) + j] = (T)p.coef[(size_t)k * p.w + j];
 }
 
 GridScale make_scale(const NufftPlan& p) {

@@ -40,17 +40,19 @@ template <typename C> __device__ __forceinline__ C cmul_si(C a, int s) {
 
 // ---------------------------------------------------------------- ES kernel
 // Weights of the W grid points l0..l0+W-1 for sub-cell offset f in [0,1]:
-// piece j is a polynomial in t = 2f-1 with coefficients c[k*W + j].
+// piece j is a polynomial in t = 2f-1 with coefficients c[k*S + j], S =
+// es_stride(W).
 template <typename T, int W>
 __device__ __forceinline__ void es_weights(T f, const EsCoef<T>& cf, T (&wt)[W]) {
   constexpr int DEG = es_degree(W);
+  constexpr int S = es_stride(W);
   const T t = T(2) * f - T(1);
 #pragma unroll
-  for (int j = 0; j < W; ++j) wt[j] = cf.c[DEG * W + j];
+  for (int j = 0; j < W; ++j) wt[j] = cf.c[DEG * S + j];
 #pragma unroll
   for (int k = DEG - 1; k >= 0; --k) {
 #pragma unroll
-    for (int j = 0; j < W; ++j) wt[j] = fma(wt[j], t, cf.c[k * W + j]);
+    for (int j = 0; j < W; ++j) wt[j] = fma(wt[j], t, cf.c[k * S + j]);
   }
 }
 
@@ -59,20 +61,21 @@ __device__ __forceinline__ void es_weights(T f, const EsCoef<T>& cf, T (&wt)[W])
 template <int W>
 __device__ __forceinline__ void es_weights_x2(float f, const EsCoef<float>& cf, float (&wt)[W]) {
   constexpr int DEG = es_degree(W);
+  constexpr int S = es_stride(W);
   constexpr int NP = W / 2;
   const float t = 2.f * f - 1.f;
   const float2 tt = make_float2(t, t);
+  const float2* c2 = reinterpret_cast<const float2*>(cf.c);   // pair j of degree k at c2[k*S/2 + j]
   float2 acc[NP > 0 ? NP : 1];
   float last = 0.f;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) acc[j] = make_float2(cf.c[DEG * W + 2 * j], cf.c[DEG * W + 2 * j + 1]);
-  if (W & 1) last = cf.c[DEG * W + W - 1];
+  for (int j = 0; j < NP; ++j) acc[j] = c2[DEG * (S / 2) + j];
+  if (W & 1) last = cf.c[DEG * S + W - 1];
 #pragma unroll
   for (int k = DEG - 1; k >= 0; --k) {
 #pragma unroll
-    for (int j = 0; j < NP; ++j)
-      acc[j] = __ffma2_rn(acc[j], tt, make_float2(cf.c[k * W + 2 * j], cf.c[k * W + 2 * j + 1]));
-    if (W & 1) last = fmaf(last, t, cf.c[k * W + W - 1]);
+    for (int j = 0; j < NP; ++j) acc[j] = __ffma2_rn(acc[j], tt, c2[k * (S / 2) + j]);
+    if (W & 1) last = fmaf(last, t, cf.c[k * S + W - 1]);
   }
 #pragma unroll
   for (int j = 0; j < NP; ++j) {

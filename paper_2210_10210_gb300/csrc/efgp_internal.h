@@ -27,6 +27,9 @@ constexpr int kWidths[] = {3, 4, 5, 6, 7, 8, 10, 12, 14, 16};
 // as constant operands (W+2 is at the accuracy plateau of the fit for the
 // upsampling factors used, set by the kernel's square-root edge).
 constexpr int es_degree(int w) { return w + 2; }
+// coefficient rows are padded to an even length, so that the pair of pieces
+// (2j, 2j+1) of every degree is one aligned 8-byte operand
+constexpr int es_stride(int w) { return w + (w & 1); }
 // Edge (fine-grid cells) of the spread tiles by which points are binned; the
 // register spread kernel gives one thread per cell of a 256-cell tile.
 constexpr int tile_edge(int d) { return d == 1 ? 256 : (d == 2 ? 16 : 8); }
@@ -75,8 +78,8 @@ double es_kernel(double z, double beta);
 // Device-side parameter blocks passed by value to kernels.
 // ---------------------------------------------------------------------------
 template <typename T>
-struct EsCoef {
-  T c[(kMaxDeg + 1) * kMaxWidth];  // coefficient k of piece j at c[k*W + j]
+struct alignas(16) EsCoef {
+  T c[(kMaxDeg + 1) * kMaxWidth];  // coefficient k of piece j at c[k*es_stride(W) + j]
   int deg;
 };
 

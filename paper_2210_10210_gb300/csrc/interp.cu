@@ -5,6 +5,9 @@
 // unfold the periodic grid into an extended real grid (the coefficients are
 // conjugate-symmetric, so the grid is real), and interpolate with the same
 // exponential-of-semicircle weights as the spread.
+#include <algorithm>
+#include <cstdint>
+
 #include "kernels.h"
 
 namespace efgp {
@@ -76,7 +79,8 @@ __global__ void __launch_bounds__(256) interp_kernel(const TC* __restrict__ z, i
       int e = l0 + off;
       e = max(0, min(e, nE - W));
       e0[a] = e;
-      es_weights<TR, W>(f, cf, wt[a]);
+      if constexpr (sizeof(TR) == 4) es_weights_x2<W>(f, cf, wt[a]);
+      else es_weights<TR, W>(f, cf, wt[a]);
     }
     TR acc = 0;
     if (D == 1) {
@@ -103,6 +107,67 @@ __global__ void __launch_bounds__(256) interp_kernel(const TC* __restrict__ z, i
           s1 += wt[1 % D][v] * s;
         }
         acc += wt[0][u] * s1;
+      }
+    }
+    mu[i] = (TV)acc;
+  }
+  if (bad) atomicOr(range_flag, 1);
+}
+
+// The same interpolation with the whole real extended grid staged in shared
+// memory once per block (grids up to kInterpSmemGrid bytes, d <= 2, FP32):
+// for many unsorted targets the W^d reads per target then hit shared memory
+// instead of one L1 line per lane per row.  One persistent block per SM.
+constexpr int kInterpSmemThreads = 1024;
+constexpr size_t kInterpSmemGrid = 200 * 1024;
+constexpr long long kInterpSmemMinTargets = 1ll << 22;
+
+template <int D, int W, typename TC, typename TV>
+__global__ void __launch_bounds__(kInterpSmemThreads, 1)
+    interp_smem_kernel(const TC* __restrict__ z, int soa, long long q, GridScale gs, int off, int nE,
+                       const float* __restrict__ E2, EsCoef<float> cf, TV* __restrict__ mu, int* range_flag) {
+  extern __shared__ __align__(16) float sgrid[];
+  const long long total = D == 1 ? (long long)nE : (long long)nE * nE;
+  long long done = 0;
+  if ((reinterpret_cast<uintptr_t>(E2) & 15) == 0) {
+    const long long n4 = total / 4;
+    for (long long i = threadIdx.x; i < n4; i += blockDim.x)
+      reinterpret_cast<float4*>(sgrid)[i] = __ldg(reinterpret_cast<const float4*>(E2) + i);
+    done = n4 * 4;
+  }
+  for (long long i = done + threadIdx.x; i < total; i += blockDim.x) sgrid[i] = __ldg(E2 + i);
+  __syncthreads();
+  bool bad = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < q; i += (long long)gridDim.x * blockDim.x) {
+    float wt[D][W];
+    int e0[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      TC za = soa ? z[(long long)a * q + i] : z[i * D + a];
+      if (!(za >= TC(0) && za <= TC(1))) {
+        bad = true;
+        za = TC(0);
+      }
+      int l0;
+      float f;
+      GridPos<TC, float>::get(za, gs, l0, f);
+      int e = l0 + off;
+      e = max(0, min(e, nE - W));
+      e0[a] = e;
+      es_weights_x2<W>(f, cf, wt[a]);
+    }
+    float acc = 0.f;
+    if (D == 1) {
+#pragma unroll
+      for (int u = 0; u < W; ++u) acc = fmaf(wt[0][u], sgrid[e0[0] + u], acc);
+    } else {
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const float* row = sgrid + (e0[0] + u) * nE + e0[D - 1];
+        float s = 0.f;
+#pragma unroll
+        for (int v = 0; v < W; ++v) s = fmaf(wt[D - 1][v], row[v], s);
+        acc = fmaf(wt[0][u], s, acc);
       }
     }
     mu[i] = (TV)acc;
@@ -157,6 +222,20 @@ static cudaError_t interp_dw(const void* z, int soa, long long q, const GridScal
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if constexpr (sizeof(TR) == 4 && D <= 2) {
+    const size_t bytes = sizeof(float) * (D == 1 ? (size_t)nE : (size_t)nE * nE);
+    if (q >= kInterpSmemMinTargets && bytes <= kInterpSmemGrid) {
+      auto k = interp_smem_kernel<D, W, TC, TV>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e != cudaSuccess) return e;
+      const int blocks = (int)std::min<long long>(nsm, (q + kInterpSmemThreads - 1) / kInterpSmemThreads);
+      k<<<blocks, kInterpSmemThreads, bytes, s>>>(reinterpret_cast<const TC*>(z), soa, q, gs, off, nE,
+                                                  reinterpret_cast<const float*>(E2),
+                                                  *reinterpret_cast<const EsCoef<float>*>(coef),
+                                                  reinterpret_cast<TV*>(mu), flag);
+      return cudaGetLastError();
+    }
+  }
   const int blocks = grid_for(q, 256, nsm * 16);
   interp_kernel<D, W, TC, TV, TR><<<blocks, 256, 0, s>>>(reinterpret_cast<const TC*>(z), soa, q, gs, off, nE,
                                                          reinterpret_cast<const TR*>(E2),

@@ -416,3 +416,27 @@ def test_injected_allocation_failure_reports_enomem(E, monkeypatch):
     h = E.setup(x, y, ek, sigma, eps)
     assert h.solve()["converged"]
     h.close()
+
+
+def test_many_targets_shared_memory_interpolation(E):
+    """q >= 2^22 targets (the mean at all training points of a large
+    problem) take the interpolation with the type-2 grid staged in shared
+    memory: it must agree with the per-target gather path on a prefix and
+    with the oracle on sampled targets."""
+    name = "matern2d_1e9"
+    rec = synthdata.config(name, n=50_000)
+    x, y, _ = synthdata.make_np(rec)
+    q = (1 << 22) + 1001
+    z = synthdata.uniform_np(rec.seed, 77, 0, 2 * q).astype(np.float32).reshape(q, 2)
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS[name])
+    h = E.setup(_dev(x), _dev(y), ek, sigma, eps)
+    h.solve()
+    zd = _dev(z)
+    mu_all = h.predict(zd).double().cpu().numpy()
+    mu_pre = h.predict(zd[:3000]).double().cpu().numpy()
+    h.close()
+    scale = np.abs(mu_all).max()
+    assert np.abs(mu_all[:3000] - mu_pre).max() <= 1e-6 * scale
+    idx = np.random.default_rng(9).choice(q, 1500, replace=False)
+    ref = _oracle((name, 50_000, "smem", 1500), x, y, z[idx].astype(np.float64), ok, sigma, eps)
+    assert np.abs(mu_all[idx] - ref.mu).max() <= 10 * eps * np.abs(y).max()
