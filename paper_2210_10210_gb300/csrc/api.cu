@@ -174,6 +174,13 @@ void fill_coef(const NufftPlan& p, EsCoef<T>* c) {
   c->deg = p.deg;
   for (int k = 0; k <= p.deg; ++k)
     for (int j = 0; j < p.w; ++j) c->c[k * es_stride(p.w) + j] = (T)p.coef[(size_t)k * p.w + j];
+  const int npr = es_pairs(p.w);
+  for (int j = 0; j < (p.w + 1) / 2; ++j)
+    for (int i = 0; i < npr; ++i)
+      for (int e = 0; e < 2; ++e) {
+        const int k = 2 * i + e;
+        c->sp[2 * (j * npr + i) + e] = k <= p.deg ? (T)p.coef[(size_t)k * p.w + j] : T(0);
+      }
 }
 
 GridScale make_scale(const NufftPlan& p) {

@@ -40,49 +40,55 @@ template <typename C> __device__ __forceinline__ C cmul_si(C a, int s) {
 
 // ---------------------------------------------------------------- ES kernel
 // Weights of the W grid points l0..l0+W-1 for sub-cell offset f in [0,1]:
-// piece j is a polynomial in t = 2f-1 with coefficients c[k*S + j], S =
-// es_stride(W).
+// piece j is a polynomial P_j in t = 2f-1.  psi is even, so P_{W-1-j}(t) =
+// P_j(-t): with P_j(t) = E_j(t^2) + t O_j(t^2) one Horner pass in t^2 over the
+// coefficient pairs gives both pieces of a pair (the host fit is exactly
+// mirror-symmetric).
 template <typename T, int W>
 __device__ __forceinline__ void es_weights(T f, const EsCoef<T>& cf, T (&wt)[W]) {
-  constexpr int DEG = es_degree(W);
-  constexpr int S = es_stride(W);
+  constexpr int NPR = es_pairs(W);
   const T t = T(2) * f - T(1);
+  const T s = t * t;
 #pragma unroll
-  for (int j = 0; j < W; ++j) wt[j] = cf.c[DEG * S + j];
+  for (int j = 0; j < (W + 1) / 2; ++j) {
+    const T* c = cf.sp + 2 * j * NPR;
+    T e = c[2 * (NPR - 1)], o = c[2 * (NPR - 1) + 1];
 #pragma unroll
-  for (int k = DEG - 1; k >= 0; --k) {
-#pragma unroll
-    for (int j = 0; j < W; ++j) wt[j] = fma(wt[j], t, cf.c[k * S + j]);
+    for (int i = NPR - 2; i >= 0; --i) {
+      e = fma(e, s, c[2 * i]);
+      o = fma(o, s, c[2 * i + 1]);
+    }
+    if (2 * j == W - 1) {
+      wt[j] = e;
+    } else {
+      wt[j] = fma(t, o, e);
+      wt[W - 1 - j] = fma(-t, o, e);
+    }
   }
 }
 
-// The same weights with pairs of pieces evaluated by packed two-lane FP32
-// FMAs (one instruction for two pieces).
+// The same weights with each (even, odd) Horner pair and each mirrored pair
+// of pieces computed by packed two-lane FP32 FMAs.
 template <int W>
 __device__ __forceinline__ void es_weights_x2(float f, const EsCoef<float>& cf, float (&wt)[W]) {
-  constexpr int DEG = es_degree(W);
-  constexpr int S = es_stride(W);
-  constexpr int NP = W / 2;
+  constexpr int NPR = es_pairs(W);
   const float t = 2.f * f - 1.f;
-  const float2 tt = make_float2(t, t);
-  const float2* c2 = reinterpret_cast<const float2*>(cf.c);   // pair j of degree k at c2[k*S/2 + j]
-  float2 acc[NP > 0 ? NP : 1];
-  float last = 0.f;
+  const float s = t * t;
+  const float2 ss = make_float2(s, s), tm = make_float2(t, -t);
+  const float2* c2 = reinterpret_cast<const float2*>(cf.sp);
 #pragma unroll
-  for (int j = 0; j < NP; ++j) acc[j] = c2[DEG * (S / 2) + j];
-  if (W & 1) last = cf.c[DEG * S + W - 1];
+  for (int j = 0; j < (W + 1) / 2; ++j) {
+    float2 eo = c2[j * NPR + NPR - 1];
 #pragma unroll
-  for (int k = DEG - 1; k >= 0; --k) {
-#pragma unroll
-    for (int j = 0; j < NP; ++j) acc[j] = __ffma2_rn(acc[j], tt, c2[k * (S / 2) + j]);
-    if (W & 1) last = fmaf(last, t, cf.c[k * S + W - 1]);
+    for (int i = NPR - 2; i >= 0; --i) eo = __ffma2_rn(eo, ss, c2[j * NPR + i]);
+    if (2 * j == W - 1) {
+      wt[j] = eo.x;
+    } else {
+      const float2 r = __ffma2_rn(tm, make_float2(eo.y, eo.y), make_float2(eo.x, eo.x));
+      wt[j] = r.x;
+      wt[W - 1 - j] = r.y;
+    }
   }
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    wt[2 * j] = acc[j].x;
-    wt[2 * j + 1] = acc[j].y;
-  }
-  if (W & 1) wt[W - 1] = last;
 }
 
 // Fine-grid position of a coordinate x in [0,1]: u = x * s, footprint start

@@ -77,9 +77,13 @@ double es_kernel(double z, double beta);
 // ---------------------------------------------------------------------------
 // Device-side parameter blocks passed by value to kernels.
 // ---------------------------------------------------------------------------
+constexpr int es_pairs(int w) { return es_degree(w) / 2 + 1; }   // (even, odd) coefficient pairs per piece
 template <typename T>
 struct alignas(16) EsCoef {
   T c[(kMaxDeg + 1) * kMaxWidth];  // coefficient k of piece j at c[k*es_stride(W) + j]
+  // pieces j < (W+1)/2 as pairs (c_{j,2i}, c_{j,2i+1}) at sp[2*(j*es_pairs(W) + i)]:
+  // piece j is E_j(t^2) + t O_j(t^2) and piece W-1-j is E_j(t^2) - t O_j(t^2)
+  T sp[2 * (kMaxWidth / 2) * (kMaxDeg / 2 + 1)];
   int deg;
 };
 

@@ -246,7 +246,11 @@ static double fit_pieces(int w, double beta, int deg, std::vector<double>& coef)
   std::vector<double> nodes(np);
   for (int i = 0; i < np; ++i) nodes[i] = std::cos(kPi * (i + 0.5) / np);
   double err = 0.0;
-  for (int j = 0; j < w; ++j) {
+  // psi is even, so piece w-1-j at t is piece j at -t: the first half of the
+  // pieces is fitted, the rest mirrored (coefficient k times (-1)^k), and the
+  // odd coefficients of a middle piece are zero -- exactly, so that the device
+  // may evaluate the pieces pairwise from their even and odd parts.
+  for (int j = 0; j < (w + 1) / 2; ++j) {
     std::vector<double> A((size_t)np * np), b(np);
     for (int i = 0; i < np; ++i) {
       double t = nodes[i], tp = 1.0;
@@ -258,11 +262,19 @@ static double fit_pieces(int w, double beta, int deg, std::vector<double>& coef)
       b[i] = es_kernel((j + f - 0.5 * w) / (0.5 * w), beta);
     }
     solve_dense(A, b, np);
-    for (int k = 0; k < np; ++k) coef[(size_t)k * w + j] = b[k];
+    const int jm = w - 1 - j;
+    if (jm == j)
+      for (int k = 1; k < np; k += 2) b[k] = 0.0;
+    for (int k = 0; k < np; ++k) {
+      coef[(size_t)k * w + j] = b[k];
+      coef[(size_t)k * w + jm] = (k & 1) ? -b[k] : b[k];
+    }
+  }
+  for (int j = 0; j < w; ++j) {
     for (int s = 0; s <= 400; ++s) {
       double t = -1.0 + 2.0 * s / 400.0;
       double p = 0.0;
-      for (int k = np - 1; k >= 0; --k) p = p * t + b[k];
+      for (int k = np - 1; k >= 0; --k) p = p * t + coef[(size_t)k * w + j];
       double f = 0.5 * (t + 1.0);
       err = std::max(err, std::fabs(p - es_kernel((j + f - 0.5 * w) / (0.5 * w), beta)));
     }
