@@ -342,6 +342,7 @@ __device__ __forceinline__ int block_excl_scan_n(int v, int* warp_tot) {
 constexpr int kTmaScatterThreads = 512;
 constexpr int kTmaScatterPPT = 8;
 constexpr int kTmaScatterChunk = kTmaScatterThreads * kTmaScatterPPT;
+constexpr int kTmaScatterMaxSlice = (kSortedScatterMaxTiles + kTmaScatterThreads - 1) / kTmaScatterThreads;
 
 template <int D>
 __global__ void __launch_bounds__(kTmaScatterThreads, 1)
@@ -410,17 +411,25 @@ __global__ void __launch_bounds__(kTmaScatterThreads, 1)
       rk[p] = atomicAdd(&hist[tt[p]], 1u);
     }
     __syncthreads();
+    // output runs: reserve each tile's run with a global fetch-add whose
+    // result is only stored after the shared-memory scatter below, so the
+    // atomics' round trip overlaps the barrier and the scatter
+    const int a0 = tid * slice, a1 = min(T, a0 + slice);
+    unsigned long long got[kTmaScatterMaxSlice];
     {
-      const int a0 = tid * slice, a1 = min(T, a0 + slice);
       int sum = 0;
       for (int i = a0; i < a1; ++i) sum += (int)hist[i];
       int run = block_excl_scan_n<NT>(sum, wtot);
-      for (int i = a0; i < a1; ++i) {
-        lstart[i] = run;
-        const unsigned int h = hist[i];
-        run += (int)h;
-        if (h) base[i] = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[i]),
-                                              (unsigned long long)h);
+#pragma unroll
+      for (int u = 0; u < kTmaScatterMaxSlice; ++u) {
+        const int i = a0 + u;
+        got[u] = 0ull;
+        if (i < a1) {
+          lstart[i] = run;
+          const unsigned int h = hist[i];
+          run += (int)h;
+          if (h) got[u] = atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[i]), (unsigned long long)h);
+        }
       }
     }
     __syncthreads();
@@ -433,6 +442,9 @@ __global__ void __launch_bounds__(kTmaScatterThreads, 1)
       sq[D * P + pos] = sx[D * P + k];
       stile[pos] = tt[p];
     }
+#pragma unroll
+    for (int u = 0; u < kTmaScatterMaxSlice; ++u)
+      if (a0 + u < a1) base[a0 + u] = (long long)got[u];
     __syncthreads();
     for (int i = tid; i < P; i += NT) {
       const int t = stile[i];
