@@ -168,6 +168,35 @@ std::vector<Pass> matvec_passes(int d, int n1, int L, size_t elem, long long* sc
   return ps;
 }
 
+// The product as captured for graph-launched CG.  In 3D, where a slab's
+// L x L transform fits in shared memory, the two inner axes of each direction
+// are one plane pass: plane forward (prologue) -> axis-0 pass with the w-hat
+// product -> plane inverse (epilogue), three launches instead of five.
+std::vector<Pass> graph_matvec_passes(int d, int n1, int L, size_t elem, const std::vector<Pass>& line_passes) {
+  if (d != 3 || plane_fft_smem_bytes(L, elem) > kLineFftBlockSmem) return line_passes;
+  std::vector<Pass> ps;
+  Pass pf = line_passes[0];
+  pf.kind = 1;
+  pf.n1 = n1;
+  pf.in_buf = 0;
+  pf.out_buf = 2;
+  pf.dir = -1;
+  pf.inm = IN_CG;
+  pf.outm = OUT_PLAIN;
+  pf.conv = false;
+  ps.push_back(pf);
+  ps.push_back(line_passes[2]);   // axis 0 on L^2 lines, product, inverse, keep n1 (S in place)
+  Pass pi = pf;
+  pi.kind = 2;
+  pi.in_buf = 2;
+  pi.out_buf = 0;
+  pi.dir = +1;
+  pi.inm = IN_PLAIN;
+  pi.outm = OUT_CG;
+  ps.push_back(pi);
+  return ps;
+}
+
 template <typename T>
 void fill_coef(const NufftPlan& p, EsCoef<T>* c) {
   std::memset(c, 0, sizeof(*c));
@@ -253,6 +282,17 @@ int run_passes(efgp_handle* H, const std::vector<Pass>& ps, void* buf0, void* bu
   if (!(cga && cga->check_done)) H->times.launches += (int64_t)ps.size();
   for (const Pass& p : ps) {
     cudaError_t e;
+    if (p.kind != 0) {
+      CgArgs c{};
+      if (cga) c = *cga;
+      void* S = bufs[p.kind == 1 ? p.out_buf : p.in_buf];
+      if (H->f64)
+        e = launch_plane_fft<double>(p.g, p.n1, p.kind == 2, S, reinterpret_cast<const double2*>(tw), c, H->stream);
+      else
+        e = launch_plane_fft<float>(p.g, p.n1, p.kind == 2, S, reinterpret_cast<const float2*>(tw), c, H->stream);
+      EFGP_CK(e);
+      continue;
+    }
     if (H->f64)
       e = launch_line_fft<double>(p.g, bufs[p.in_buf], bufs[p.out_buf], p.dir, reinterpret_cast<const double2*>(tw),
                                   p.conv ? reinterpret_cast<const double*>(what) : nullptr, p.inm, p.outm, cga,
@@ -614,9 +654,15 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   return EFGP_OK;
 }
 
-int capture_cg_graph(efgp_handle* H) {
-  if (H->graph) return EFGP_OK;
-  const int iters = H->opt.iters_per_launch > 0 ? H->opt.iters_per_launch : 32;
+// Blocks of a pass's launch.
+long long pass_blocks(const Pass& p) { return p.kind ? p.n1 : (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb; }
+
+// CG arguments of the graph-launched iteration.  With cg_fuse = 1 (d >= 2)
+// the iteration is fused: the w-hat product pass computes p^H A p by Parseval
+// and alpha, and the last pass updates x and r, so no separate vector-update
+// kernel runs (one launch fewer, but the updates then run on the last pass's
+// blocks only: measured slower at the configured sizes, hence not default).
+CgArgs graph_cg_args(efgp_handle* H, const std::vector<Pass>& ps) {
   CgArgs cga{};
   cga.src = H->p;
   cga.r = H->r;
@@ -628,12 +674,26 @@ int capture_cg_graph(efgp_handle* H) {
   cga.update_p = 1;
   cga.do_dot = 1;
   cga.check_done = 1;
+  if (H->d >= 2 && H->opt.cg_fuse == 1 && ps.size() >= 3) {
+    cga.fused = 1;
+    cga.n_pre = (int)pass_blocks(ps.front());
+    cga.partials2 = H->partials2;
+    cga.x = H->x;
+    cga.rw = H->r;
+  }
+  return cga;
+}
+
+int capture_cg_graph(efgp_handle* H) {
+  if (H->graph) return EFGP_OK;
+  const int iters = H->opt.iters_per_launch > 0 ? H->opt.iters_per_launch : 32;
+  const CgArgs cga = graph_cg_args(H, H->mvg);
   cudaGraph_t g = nullptr;
   EFGP_CK(cudaStreamBeginCapture(H->stream, cudaStreamCaptureModeThreadLocal));
   int rc = EFGP_OK;
   for (int it = 0; it < iters && rc == EFGP_OK; ++it) {
-    rc = run_passes(H, H->mv, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
-    if (rc == EFGP_OK) {
+    rc = run_passes(H, H->mvg, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
+    if (rc == EFGP_OK && !cga.fused) {
       cudaError_t e = launch_cg_update(H->x, H->r, H->p, H->Ap, H->M, H->st, H->partials, H->stream);
       if (e != cudaSuccess) {
         set_error(std::string("cg update: ") + cudaGetErrorString(e));
@@ -868,7 +928,7 @@ int apply_system_dev(efgp_handle* H, double2* in, double2* out) {
   cga.update_p = 0;
   cga.do_dot = 0;
   cga.check_done = 0;
-  return run_passes(H, H->mv, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
+  return run_passes(H, H->mvg, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
 }
 
 int handle_init(efgp_handle* H, int d, long long N, const efgp_kernel* kern, double sigma, double eps,
@@ -897,6 +957,8 @@ int handle_init(efgp_handle* H, int d, long long N, const efgp_kernel* kern, dou
   pool_init(H->device);
   EFGP_CK(prepare_line_fft<float>());
   EFGP_CK(prepare_line_fft<double>());
+  EFGP_CK(prepare_plane_fft<float>());
+  EFGP_CK(prepare_plane_fft<double>());
   if (o.stream) {
     H->stream = (cudaStream_t)o.stream;
   } else {
@@ -933,9 +995,13 @@ int handle_init(efgp_handle* H, int d, long long N, const efgp_kernel* kern, dou
   EFGP_CK(cudaMemsetAsync(H->x, 0, sizeof(double2) * M, H->stream));
   long long scratch = 1;
   H->mv = matvec_passes(d, H->n1, L, H->elem, &scratch);
+  H->mvg = graph_matvec_passes(d, H->n1, L, H->elem, H->mv);
   long long maxblocks = 1024;
   for (const Pass& p : H->mv) maxblocks = std::max(maxblocks, (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb);
+  for (const Pass& p : H->mvg)
+    maxblocks = std::max<long long>(maxblocks, p.kind ? p.n1 : (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb);
   EFGP_TRY(H->alloc((void**)&H->partials, sizeof(double) * (maxblocks + 16)));
+  EFGP_TRY(H->alloc((void**)&H->partials2, sizeof(double) * (maxblocks + 16)));
   EFGP_TRY(H->alloc(&H->scrA, H->elem * scratch));
   EFGP_TRY(H->alloc(&H->scrB, H->elem * scratch));
   EFGP_TRY(H->alloc((void**)&H->flag, sizeof(int) * 4));
@@ -1090,7 +1156,7 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   while (true) {
     EFGP_CK(cudaGraphLaunch(H->graph, H->stream));
     launched += H->graph_iters;
-    H->times.launches += (int64_t)H->graph_iters * ((int64_t)H->mv.size() + 1);
+    H->times.launches += (int64_t)H->graph_iters * ((int64_t)H->mvg.size() + (H->d >= 2 && H->opt.cg_fuse == 1 ? 0 : 1));
     EFGP_CK(cudaMemcpyAsync(H->host_state, H->st, sizeof(CgState), cudaMemcpyDeviceToHost, H->stream));
     EFGP_CK(cudaStreamSynchronize(H->stream));
     if (H->host_state->done) break;
@@ -1470,7 +1536,7 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
       cga.do_dot = 1;
       cga.check_done = 1;
       for (int it = 0; it < iters && rc == EFGP_OK; ++it) {
-        rc = run_passes(H, H->mv, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
+        rc = run_passes(H, H->mvg, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
         if (rc == EFGP_OK && launch_cg_update(H->x, H->r, H->p, H->Ap, H->M, H->st, H->partials, H->stream) !=
                                  cudaSuccess)
           rc = EFGP_ECUDA;

@@ -23,6 +23,84 @@
 
 namespace efgp {
 
+// p^H A p over the grid from each thread's part: per-block partials, summed in
+// block order by the block that arrives last, which sets alpha = r^H r / p^H A p.
+// (Fused iteration: the product pass's partials plus the first pass's
+// sigma^2 |p|^2 partials give p^H A p.)
+__device__ void pap_reduce(double dot, const CgArgs& cga, double* red) {
+  const double bs = block_sum(dot, red);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    cga.partials[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned int t = atomicAdd(&cga.st->ticket_a, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double tot = block_sum_partials(cga.partials, gridDim.x, red);
+    if (cga.fused) tot += block_sum_partials(cga.partials2, cga.n_pre, red);
+    if (threadIdx.x == 0) {
+      CgState* st = cga.st;
+      st->pAp = tot;
+      if (!(tot > 0.0) || !isfinite(tot)) {
+        st->alpha = 0.0;
+        st->done = 3;   // breakdown: p^H A p not positive
+      } else {
+        st->alpha = st->rr / tot;
+      }
+      st->ticket_a = 0u;
+    }
+  }
+}
+
+// Fused iteration, first pass: this block's sigma^2 |p|^2 into partials2.
+__device__ void pre_store(double v, const CgArgs& cga, double* red) {
+  const double bs = block_sum(v, red);
+  if (threadIdx.x == 0) cga.partials2[blockIdx.x] = bs;
+}
+
+// Fused iteration, last pass: r^H r of the updated residual (deterministic
+// two-level sum), then beta and the convergence test, as in the CG update.
+__device__ void rr_reduce(double dot, const CgArgs& cga, double* red) {
+  const double bs = block_sum(dot, red);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    cga.partials[blockIdx.x] = bs;
+    __threadfence();
+    last = (atomicAdd(&cga.st->ticket_b, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    const double tot = block_sum_partials(cga.partials, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      CgState* st = cga.st;
+      st->rr_new = tot;
+      st->iter += 1;
+      st->beta = tot / st->rr;
+      st->rr = tot;
+      if (!isfinite(tot)) st->done = 3;
+      else if (tot <= st->tol2) st->done = 1;
+      else if (st->iter >= st->max_iter) st->done = 2;
+      st->ticket_b = 0u;
+    }
+  }
+}
+
+// The pass's share of the CG bookkeeping after its line batch.
+template <int INM, int OUTM, bool CONV>
+__device__ __forceinline__ void pass_reduce(double v, const CgArgs& cga, double* red) {
+  if (cga.fused) {
+    if (OUTM == OUT_CG) rr_reduce(v, cga, red);
+    else if (CONV) pap_reduce(v, cga, red);
+    else if (INM == IN_CG) pre_store(v, cga, red);
+  } else if (OUTM == OUT_CG && cga.do_dot) {
+    pap_reduce(v, cga, red);
+  }
+}
+
 template <typename T, int INM, int OUTM, bool CONV>
 __global__ void __launch_bounds__(kLineFftMaxThreads) line_fft_kernel(LineGeom g, const void* __restrict__ in_v, void* out_v, int dir,
                                                        const cplx<T>* __restrict__ tw, const T* __restrict__ what,
@@ -30,41 +108,160 @@ __global__ void __launch_bounds__(kLineFftMaxThreads) line_fft_kernel(LineGeom g
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   grid_dependency_wait();
-  if (INM == IN_CG || OUTM == OUT_CG) {
+  // (plain passes skip the state read: one dependent load on every
+  // iteration's critical path costs more than the few passes run after
+  // convergence inside a captured group)
+  if (INM == IN_CG || OUTM == OUT_CG || (CONV && cga.fused)) {
     if (cga.check_done && cga.st->done) return;
   }
   double cg_beta = 0.0;
   if (INM == IN_CG && cga.update_p) cg_beta = cga.st->beta;
-  const double dot = line_block<T, INM, OUTM, CONV>(g, blockIdx.x, in_v, out_v, dir, tw, what, cga, cg_beta, smem_raw);
-  if (OUTM == OUT_CG && cga.do_dot) {
-    const double bs = block_sum(dot, red);
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-      cga.partials[blockIdx.x] = bs;
-      __threadfence();
-      const unsigned int t = atomicAdd(&cga.st->ticket_a, 1u);
-      last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      const double tot = block_sum_partials(cga.partials, gridDim.x, red);
-      if (threadIdx.x == 0) {
-        CgState* st = cga.st;
-        st->pAp = tot;
-        if (!(tot > 0.0) || !isfinite(tot)) {
-          st->alpha = 0.0;
-          st->done = 3;   // breakdown: p^H A p not positive
-        } else {
-          st->alpha = st->rr / tot;
-        }
-        st->ticket_a = 0u;
-      }
-    }
-  }
+  if (OUTM == OUT_CG && cga.fused) cg_beta = cga.st->alpha;   // the fused epilogue's step length
+  const double v = line_block<T, INM, OUTM, CONV>(g, blockIdx.x, in_v, out_v, dir, tw, what, cga, cg_beta, smem_raw);
+  pass_reduce<INM, OUTM, CONV>(v, cga, red);
 }
 
 size_t line_fft_smem_bytes(int L, int nb, size_t elem_bytes) { return 2 * (size_t)nb * (L + 1) * elem_bytes; }
+
+// ---- 3D Toeplitz product, inner two axes of one slab per block.
+// The CG vector is [j0][j1][j2] (n1^3); the scratch S holds [j0][k1][k2]
+// (n1 x L x L) between the forward plane pass, the axis-0 pass with the
+// w-hat product, and the inverse plane pass.  A block takes slab j0: its
+// n1 x n1 values are FFT'd along axis 2 (n1 rows, padded to L), transposed in
+// shared memory and FFT'd along axis 1 (L rows); the inverse pass mirrors it
+// and keeps the first n1 entries of each axis.
+
+// forward: CG prologue (p = r + beta p, times D) -> S
+template <typename T>
+__global__ void __launch_bounds__(kPlaneThreads) plane_fwd_kernel(LineGeom g, int n1, cplx<T>* __restrict__ S,
+                                                                  const cplx<T>* __restrict__ tw, CgArgs cga) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  grid_dependency_wait();
+  if (cga.check_done && cga.st->done) return;
+  const double beta = cga.update_p ? cga.st->beta : 0.0;
+  const int L = g.L, LP = L + 1;
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* b1 = b0 + (size_t)L * LP;
+  const long long j0 = blockIdx.x;
+  const long long base = j0 * n1 * n1;
+  const float rL = 1.0f / (float)L;
+  double pre = 0.0;
+  for (int e = threadIdx.x; e < n1 * L; e += blockDim.x) {
+    const int j1 = quick_div(e, L, rL), k = e - j1 * L;
+    cplx<T> v = mk<T>(0, 0);
+    if (k < n1) {
+      const long long j = base + (long long)j1 * n1 + k;
+      double2 pv = __ldcg(cga.src + j);
+      if (cga.update_p) {
+        const double2 rv = __ldcg(cga.r + j);
+        pv.x = rv.x + beta * pv.x;
+        pv.y = rv.y + beta * pv.y;
+        cga.src[j] = pv;
+      }
+      const double dj = cga.Dw[j];
+      v = mk<T>((T)(dj * pv.x), (T)(dj * pv.y));
+      if (cga.fused) pre += cga.sigma2 * (pv.x * pv.x + pv.y * pv.y);
+    }
+    b0[j1 * LP + k] = v;
+  }
+  __syncthreads();
+  cplx<T>* r = stockham_all<T>(b0, b1, g, LP, n1, -1, tw);   // axis 2, rows j1 < n1
+  cplx<T>* o = (r == b0) ? b1 : b0;
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+    const int k2 = quick_div(e, L, rL), j1 = e - k2 * L;
+    o[k2 * LP + j1] = j1 < n1 ? r[j1 * LP + k2] : mk<T>(0, 0);
+  }
+  __syncthreads();
+  cplx<T>* r2 = stockham_all<T>(o, r, g, LP, L, -1, tw);     // axis 1, rows k2 < L
+  cplx<T>* out = S + j0 * L * L;
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+    const int k1 = quick_div(e, L, rL), k2 = e - k1 * L;
+    out[e] = r2[k2 * LP + k1];
+  }
+  if (cga.fused) {
+    __shared__ double red[32];
+    pre_store(pre, cga, red);
+  }
+}
+
+// inverse: S -> CG epilogue (A p = D v + sigma^2 p) and the p^H A p reduction
+template <typename T>
+__global__ void __launch_bounds__(kPlaneThreads) plane_inv_kernel(LineGeom g, int n1, const cplx<T>* __restrict__ S,
+                                                                  const cplx<T>* __restrict__ tw, CgArgs cga) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  grid_dependency_wait();
+  if (cga.check_done && cga.st->done) return;
+  const double alpha = cga.fused ? cga.st->alpha : 0.0;
+  const int L = g.L, LP = L + 1;
+  cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* b1 = b0 + (size_t)L * LP;
+  const long long j0 = blockIdx.x;
+  const float rL = 1.0f / (float)L, rn1 = 1.0f / (float)n1;
+  const cplx<T>* in = S + j0 * L * L;
+  for (int e = threadIdx.x; e < L * L; e += blockDim.x) {
+    const int k1 = quick_div(e, L, rL), k2 = e - k1 * L;
+    b0[k1 * LP + k2] = __ldcg(in + e);
+  }
+  __syncthreads();
+  cplx<T>* r = stockham_all<T>(b0, b1, g, LP, L, +1, tw);    // axis 2, rows k1 < L
+  cplx<T>* o = (r == b0) ? b1 : b0;
+  for (int e = threadIdx.x; e < n1 * L; e += blockDim.x) {
+    const int j2 = quick_div(e, L, rL), k1 = e - j2 * L;
+    o[j2 * LP + k1] = r[k1 * LP + j2];
+  }
+  __syncthreads();
+  cplx<T>* r2 = stockham_all<T>(o, r, g, LP, n1, +1, tw);    // axis 1, rows j2 < n1
+  double dot = 0.0;
+  const long long base = j0 * n1 * n1;
+  for (int e = threadIdx.x; e < n1 * n1; e += blockDim.x) {
+    const int j1 = quick_div(e, n1, rn1), j2 = e - j1 * n1;
+    const cplx<T> v = r2[j2 * LP + j1];
+    const long long j = base + e;
+    const double dj = cga.Dw[j];
+    const double2 sv = __ldcg(cga.src + j);
+    double2 a;
+    a.x = dj * (double)v.x + cga.sigma2 * sv.x;
+    a.y = dj * (double)v.y + cga.sigma2 * sv.y;
+    if (cga.fused) {
+      dot += cg_fused_update(cga, j, sv, a, alpha);
+    } else {
+      cga.dst[j] = a;
+      dot += sv.x * a.x + sv.y * a.y;
+    }
+  }
+  __syncthreads();
+  if (cga.fused) rr_reduce(dot, cga, red);
+  else if (cga.do_dot) pap_reduce(dot, cga, red);
+}
+
+size_t plane_fft_smem_bytes(int L, size_t elem_bytes) { return 2 * (size_t)L * (L + 1) * elem_bytes; }
+
+template <typename T>
+cudaError_t launch_plane_fft(const LineGeom& g, int n1, int inverse, void* S, const cplx<T>* tw, const CgArgs& cga,
+                             cudaStream_t s) {
+  const size_t smem = plane_fft_smem_bytes(g.L, sizeof(cplx<T>));
+  if (inverse)
+    return launch_pdl(plane_inv_kernel<T>, dim3((unsigned)n1), dim3(kPlaneThreads), smem, s, g, n1,
+                      reinterpret_cast<const cplx<T>*>(S), tw, cga);
+  return launch_pdl(plane_fwd_kernel<T>, dim3((unsigned)n1), dim3(kPlaneThreads), smem, s, g, n1,
+                    reinterpret_cast<cplx<T>*>(S), tw, cga);
+}
+template cudaError_t launch_plane_fft<float>(const LineGeom&, int, int, void*, const float2*, const CgArgs&,
+                                             cudaStream_t);
+template cudaError_t launch_plane_fft<double>(const LineGeom&, int, int, void*, const double2*, const CgArgs&,
+                                              cudaStream_t);
+
+template <typename T>
+cudaError_t prepare_plane_fft() {
+  cudaError_t e = cudaFuncSetAttribute(plane_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kLineFftBlockSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(plane_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kLineFftBlockSmem);
+}
+template cudaError_t prepare_plane_fft<float>();
+template cudaError_t prepare_plane_fft<double>();
 
 template <typename T, int INM, int OUTM, bool CONV>
 static cudaError_t launch_one(const LineGeom& g, const void* in, void* out, int dir, const cplx<T>* tw, const T* what,

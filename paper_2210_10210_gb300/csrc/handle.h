@@ -20,6 +20,8 @@ struct Pass {
   int inm, outm;
   bool conv;
   int threads;
+  int kind = 0;   // 0 line batches; 1, 2: forward, inverse plane pass of the 3D product
+  int n1 = 0;     // plane passes: data extent per axis
 };
 
 bool fault_injected(const char* what);
@@ -58,6 +60,7 @@ struct efgp_handle {
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
   CgState* st = nullptr;
   double* partials = nullptr;
+  double* partials2 = nullptr;   // first-pass partial sums of the fused CG iteration
   void* scrA = nullptr;
   void* scrB = nullptr;
   void* g2 = nullptr;
@@ -70,6 +73,7 @@ struct efgp_handle {
   char* pinned = nullptr;   // 256-byte pinned slot holding host_state and host_flag
   // plans
   std::vector<Pass> mv;
+  std::vector<Pass> mvg;   // the product as captured in the CG graph (3D: plane passes where they fit)
   std::vector<Pass> fft2;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;

@@ -20,6 +20,15 @@ struct CgArgs {
   int update_p;          // 1: first pass sets src = r + beta*src (iteration > 0)
   int do_dot;            // 1: last pass reduces Re(src^H dst) into st->pAp, alpha
   int check_done;        // 1: skip everything once st->done is set
+  // Fused iteration (graph-launched CG, d >= 2): the first pass reduces
+  // sigma^2 |p|^2 into partials2, the w-hat product pass adds
+  // sum_k w-hat_k |FFT(D p)_k|^2 (= (Dp)^H T (Dp) by Parseval) and sets
+  // alpha, and the last pass updates x and r itself and reduces r^H r.
+  int fused;
+  int n_pre;             // blocks of the first pass (entries of partials2)
+  double* partials2;
+  double2* x;            // fused: solution and residual updated by the last pass
+  double2* rw;
 };
 
 enum LineIn { IN_PLAIN = 0, IN_CG = 1 };
@@ -34,6 +43,17 @@ cudaError_t launch_line_fft(const LineGeom& g, const void* in, void* out, int di
                             int inm, int outm, const CgArgs* cga, int threads, cudaStream_t s);
 
 size_t line_fft_smem_bytes(int L, int nb, size_t elem_bytes);
+
+// 3D Toeplitz product, inner two axes per slab (one block per j0 < n1): the
+// forward pass reads the CG vector (prologue) and writes S [n1][L][L]; the
+// inverse pass reads S and applies the CG epilogue and reduction.
+constexpr int kPlaneThreads = 512;
+size_t plane_fft_smem_bytes(int L, size_t elem_bytes);
+template <typename T>
+cudaError_t launch_plane_fft(const LineGeom& g, int n1, int inverse, void* S, const cplx<T>* tw, const CgArgs& cga,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t prepare_plane_fft();
 constexpr int kLineFftMaxSmem = 200 * 1024;   // dynamic shared memory cap of one pass
 constexpr size_t kLineFftBlockSmem = 100 * 1024;   // preferred cap (two blocks per SM)
 constexpr int kLineFftMaxThreads = 512;
