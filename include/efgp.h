@@ -91,10 +91,6 @@ typedef struct {
                         /*    (small problems);                                            */
                         /* 3: one launch whose blocks claim work items (FFT line batches,   */
                         /*    vector chunks) of any problem's current CG phase             */
-  int cg_fuse;          /* graph-launched CG, d >= 2: 1 fuses the iteration into the       */
-                        /* Toeplitz passes (p^H A p by Parseval in the w-hat product pass, */
-                        /* x and r updated by the last pass); 0 or 2: separate update      */
-                        /* kernel (default; faster at the sizes measured)                  */
   void* stream;         /* cudaStream_t to order work on (NULL: a private stream)         */
 } efgp_options;
 

@@ -23,7 +23,7 @@ class efgp_options(C.Structure):
                 ("host_io", C.c_int), ("cg_tol", C.c_double), ("max_iter", C.c_int64), ("nufft_tol", C.c_double),
                 ("m_override", C.c_int), ("h_override", C.c_double), ("fft_len_override", C.c_int),
                 ("upsampfac", C.c_double), ("es_width", C.c_int), ("iters_per_launch", C.c_int),
-                ("autotune", C.c_int), ("profile", C.c_int), ("cg_mode", C.c_int), ("cg_fuse", C.c_int),
+                ("autotune", C.c_int), ("profile", C.c_int), ("cg_mode", C.c_int),
                 ("stream", C.c_void_p)]
 
 

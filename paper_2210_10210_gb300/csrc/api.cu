@@ -276,6 +276,9 @@ double default_rho(double eps) { return eps / 10.0; }
 // ---------------------------------------------------------------------------
 namespace {
 
+// Blocks of a pass's launch.
+long long pass_blocks(const Pass& p) { return p.kind ? p.n1 : (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb; }
+
 int run_passes(efgp_handle* H, const std::vector<Pass>& ps, void* buf0, void* buf1, void* buf2, const void* what,
                const void* tw, const CgArgs* cga) {
   void* bufs[3] = {buf0, buf1, buf2};
@@ -654,15 +657,9 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   return EFGP_OK;
 }
 
-// Blocks of a pass's launch.
-long long pass_blocks(const Pass& p) { return p.kind ? p.n1 : (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb; }
-
-// CG arguments of the graph-launched iteration.  With cg_fuse = 1 (d >= 2)
-// the iteration is fused: the w-hat product pass computes p^H A p by Parseval
-// and alpha, and the last pass updates x and r, so no separate vector-update
-// kernel runs (one launch fewer, but the updates then run on the last pass's
-// blocks only: measured slower at the configured sizes, hence not default).
-CgArgs graph_cg_args(efgp_handle* H, const std::vector<Pass>& ps) {
+int capture_cg_graph(efgp_handle* H) {
+  if (H->graph) return EFGP_OK;
+  const int iters = H->opt.iters_per_launch > 0 ? H->opt.iters_per_launch : 32;
   CgArgs cga{};
   cga.src = H->p;
   cga.r = H->r;
@@ -674,26 +671,12 @@ CgArgs graph_cg_args(efgp_handle* H, const std::vector<Pass>& ps) {
   cga.update_p = 1;
   cga.do_dot = 1;
   cga.check_done = 1;
-  if (H->d >= 2 && H->opt.cg_fuse == 1 && ps.size() >= 3) {
-    cga.fused = 1;
-    cga.n_pre = (int)pass_blocks(ps.front());
-    cga.partials2 = H->partials2;
-    cga.x = H->x;
-    cga.rw = H->r;
-  }
-  return cga;
-}
-
-int capture_cg_graph(efgp_handle* H) {
-  if (H->graph) return EFGP_OK;
-  const int iters = H->opt.iters_per_launch > 0 ? H->opt.iters_per_launch : 32;
-  const CgArgs cga = graph_cg_args(H, H->mvg);
   cudaGraph_t g = nullptr;
   EFGP_CK(cudaStreamBeginCapture(H->stream, cudaStreamCaptureModeThreadLocal));
   int rc = EFGP_OK;
   for (int it = 0; it < iters && rc == EFGP_OK; ++it) {
     rc = run_passes(H, H->mvg, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
-    if (rc == EFGP_OK && !cga.fused) {
+    if (rc == EFGP_OK) {
       cudaError_t e = launch_cg_update(H->x, H->r, H->p, H->Ap, H->M, H->st, H->partials, H->stream);
       if (e != cudaSuccess) {
         set_error(std::string("cg update: ") + cudaGetErrorString(e));
@@ -997,11 +980,9 @@ int handle_init(efgp_handle* H, int d, long long N, const efgp_kernel* kern, dou
   H->mv = matvec_passes(d, H->n1, L, H->elem, &scratch);
   H->mvg = graph_matvec_passes(d, H->n1, L, H->elem, H->mv);
   long long maxblocks = 1024;
-  for (const Pass& p : H->mv) maxblocks = std::max(maxblocks, (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb);
-  for (const Pass& p : H->mvg)
-    maxblocks = std::max<long long>(maxblocks, p.kind ? p.n1 : (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb);
+  for (const Pass& p : H->mv) maxblocks = std::max(maxblocks, pass_blocks(p));
+  for (const Pass& p : H->mvg) maxblocks = std::max(maxblocks, pass_blocks(p));
   EFGP_TRY(H->alloc((void**)&H->partials, sizeof(double) * (maxblocks + 16)));
-  EFGP_TRY(H->alloc((void**)&H->partials2, sizeof(double) * (maxblocks + 16)));
   EFGP_TRY(H->alloc(&H->scrA, H->elem * scratch));
   EFGP_TRY(H->alloc(&H->scrB, H->elem * scratch));
   EFGP_TRY(H->alloc((void**)&H->flag, sizeof(int) * 4));
@@ -1156,7 +1137,7 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   while (true) {
     EFGP_CK(cudaGraphLaunch(H->graph, H->stream));
     launched += H->graph_iters;
-    H->times.launches += (int64_t)H->graph_iters * ((int64_t)H->mvg.size() + (H->d >= 2 && H->opt.cg_fuse == 1 ? 0 : 1));
+    H->times.launches += (int64_t)H->graph_iters * ((int64_t)H->mvg.size() + 1);
     EFGP_CK(cudaMemcpyAsync(H->host_state, H->st, sizeof(CgState), cudaMemcpyDeviceToHost, H->stream));
     EFGP_CK(cudaStreamSynchronize(H->stream));
     if (H->host_state->done) break;

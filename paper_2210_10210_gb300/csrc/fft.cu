@@ -25,8 +25,6 @@ namespace efgp {
 
 // p^H A p over the grid from each thread's part: per-block partials, summed in
 // block order by the block that arrives last, which sets alpha = r^H r / p^H A p.
-// (Fused iteration: the product pass's partials plus the first pass's
-// sigma^2 |p|^2 partials give p^H A p.)
 __device__ void pap_reduce(double dot, const CgArgs& cga, double* red) {
   const double bs = block_sum(dot, red);
   __shared__ bool last;
@@ -39,8 +37,7 @@ __device__ void pap_reduce(double dot, const CgArgs& cga, double* red) {
   __syncthreads();
   if (last) {
     __threadfence();
-    double tot = block_sum_partials(cga.partials, gridDim.x, red);
-    if (cga.fused) tot += block_sum_partials(cga.partials2, cga.n_pre, red);
+    const double tot = block_sum_partials(cga.partials, gridDim.x, red);
     if (threadIdx.x == 0) {
       CgState* st = cga.st;
       st->pAp = tot;
@@ -55,52 +52,6 @@ __device__ void pap_reduce(double dot, const CgArgs& cga, double* red) {
   }
 }
 
-// Fused iteration, first pass: this block's sigma^2 |p|^2 into partials2.
-__device__ void pre_store(double v, const CgArgs& cga, double* red) {
-  const double bs = block_sum(v, red);
-  if (threadIdx.x == 0) cga.partials2[blockIdx.x] = bs;
-}
-
-// Fused iteration, last pass: r^H r of the updated residual (deterministic
-// two-level sum), then beta and the convergence test, as in the CG update.
-__device__ void rr_reduce(double dot, const CgArgs& cga, double* red) {
-  const double bs = block_sum(dot, red);
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    cga.partials[blockIdx.x] = bs;
-    __threadfence();
-    last = (atomicAdd(&cga.st->ticket_b, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) {
-    __threadfence();
-    const double tot = block_sum_partials(cga.partials, gridDim.x, red);
-    if (threadIdx.x == 0) {
-      CgState* st = cga.st;
-      st->rr_new = tot;
-      st->iter += 1;
-      st->beta = tot / st->rr;
-      st->rr = tot;
-      if (!isfinite(tot)) st->done = 3;
-      else if (tot <= st->tol2) st->done = 1;
-      else if (st->iter >= st->max_iter) st->done = 2;
-      st->ticket_b = 0u;
-    }
-  }
-}
-
-// The pass's share of the CG bookkeeping after its line batch.
-template <int INM, int OUTM, bool CONV>
-__device__ __forceinline__ void pass_reduce(double v, const CgArgs& cga, double* red) {
-  if (cga.fused) {
-    if (OUTM == OUT_CG) rr_reduce(v, cga, red);
-    else if (CONV) pap_reduce(v, cga, red);
-    else if (INM == IN_CG) pre_store(v, cga, red);
-  } else if (OUTM == OUT_CG && cga.do_dot) {
-    pap_reduce(v, cga, red);
-  }
-}
-
 template <typename T, int INM, int OUTM, bool CONV>
 __global__ void __launch_bounds__(kLineFftMaxThreads) line_fft_kernel(LineGeom g, const void* __restrict__ in_v, void* out_v, int dir,
                                                        const cplx<T>* __restrict__ tw, const T* __restrict__ what,
@@ -111,14 +62,13 @@ __global__ void __launch_bounds__(kLineFftMaxThreads) line_fft_kernel(LineGeom g
   // (plain passes skip the state read: one dependent load on every
   // iteration's critical path costs more than the few passes run after
   // convergence inside a captured group)
-  if (INM == IN_CG || OUTM == OUT_CG || (CONV && cga.fused)) {
+  if (INM == IN_CG || OUTM == OUT_CG) {
     if (cga.check_done && cga.st->done) return;
   }
   double cg_beta = 0.0;
   if (INM == IN_CG && cga.update_p) cg_beta = cga.st->beta;
-  if (OUTM == OUT_CG && cga.fused) cg_beta = cga.st->alpha;   // the fused epilogue's step length
-  const double v = line_block<T, INM, OUTM, CONV>(g, blockIdx.x, in_v, out_v, dir, tw, what, cga, cg_beta, smem_raw);
-  pass_reduce<INM, OUTM, CONV>(v, cga, red);
+  const double dot = line_block<T, INM, OUTM, CONV>(g, blockIdx.x, in_v, out_v, dir, tw, what, cga, cg_beta, smem_raw);
+  if (OUTM == OUT_CG && cga.do_dot) pap_reduce(dot, cga, red);
 }
 
 size_t line_fft_smem_bytes(int L, int nb, size_t elem_bytes) { return 2 * (size_t)nb * (L + 1) * elem_bytes; }
@@ -145,7 +95,6 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_fwd_kernel(LineGeom g, in
   const long long j0 = blockIdx.x;
   const long long base = j0 * n1 * n1;
   const float rL = 1.0f / (float)L;
-  double pre = 0.0;
   for (int e = threadIdx.x; e < n1 * L; e += blockDim.x) {
     const int j1 = quick_div(e, L, rL), k = e - j1 * L;
     cplx<T> v = mk<T>(0, 0);
@@ -160,7 +109,6 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_fwd_kernel(LineGeom g, in
       }
       const double dj = cga.Dw[j];
       v = mk<T>((T)(dj * pv.x), (T)(dj * pv.y));
-      if (cga.fused) pre += cga.sigma2 * (pv.x * pv.x + pv.y * pv.y);
     }
     b0[j1 * LP + k] = v;
   }
@@ -178,10 +126,6 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_fwd_kernel(LineGeom g, in
     const int k1 = quick_div(e, L, rL), k2 = e - k1 * L;
     out[e] = r2[k2 * LP + k1];
   }
-  if (cga.fused) {
-    __shared__ double red[32];
-    pre_store(pre, cga, red);
-  }
 }
 
 // inverse: S -> CG epilogue (A p = D v + sigma^2 p) and the p^H A p reduction
@@ -192,7 +136,6 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_inv_kernel(LineGeom g, in
   __shared__ double red[32];
   grid_dependency_wait();
   if (cga.check_done && cga.st->done) return;
-  const double alpha = cga.fused ? cga.st->alpha : 0.0;
   const int L = g.L, LP = L + 1;
   cplx<T>* b0 = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* b1 = b0 + (size_t)L * LP;
@@ -223,16 +166,11 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_inv_kernel(LineGeom g, in
     double2 a;
     a.x = dj * (double)v.x + cga.sigma2 * sv.x;
     a.y = dj * (double)v.y + cga.sigma2 * sv.y;
-    if (cga.fused) {
-      dot += cg_fused_update(cga, j, sv, a, alpha);
-    } else {
-      cga.dst[j] = a;
-      dot += sv.x * a.x + sv.y * a.y;
-    }
+    cga.dst[j] = a;
+    dot += sv.x * a.x + sv.y * a.y;
   }
   __syncthreads();
-  if (cga.fused) rr_reduce(dot, cga, red);
-  else if (cga.do_dot) pap_reduce(dot, cga, red);
+  if (cga.do_dot) pap_reduce(dot, cga, red);
 }
 
 size_t plane_fft_smem_bytes(int L, size_t elem_bytes) { return 2 * (size_t)L * (L + 1) * elem_bytes; }

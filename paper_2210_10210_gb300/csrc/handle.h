@@ -60,7 +60,6 @@ struct efgp_handle {
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
   CgState* st = nullptr;
   double* partials = nullptr;
-  double* partials2 = nullptr;   // first-pass partial sums of the fused CG iteration
   void* scrA = nullptr;
   void* scrB = nullptr;
   void* g2 = nullptr;

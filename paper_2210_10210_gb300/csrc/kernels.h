@@ -20,15 +20,6 @@ struct CgArgs {
   int update_p;          // 1: first pass sets src = r + beta*src (iteration > 0)
   int do_dot;            // 1: last pass reduces Re(src^H dst) into st->pAp, alpha
   int check_done;        // 1: skip everything once st->done is set
-  // Fused iteration (graph-launched CG, d >= 2): the first pass reduces
-  // sigma^2 |p|^2 into partials2, the w-hat product pass adds
-  // sum_k w-hat_k |FFT(D p)_k|^2 (= (Dp)^H T (Dp) by Parseval) and sets
-  // alpha, and the last pass updates x and r itself and reduces r^H r.
-  int fused;
-  int n_pre;             // blocks of the first pass (entries of partials2)
-  double* partials2;
-  double2* x;            // fused: solution and residual updated by the last pass
-  double2* rw;
 };
 
 enum LineIn { IN_PLAIN = 0, IN_CG = 1 };

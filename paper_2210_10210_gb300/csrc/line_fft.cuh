@@ -222,20 +222,6 @@ __device__ cplx<T>* stockham_all(cplx<T>* b0, cplx<T>* b1, const LineGeom& g, in
 // prologue), transform (optionally forward, product, inverse), store the
 // first n_out entries (optionally the CG epilogue).  Returns this thread's
 // part of Re(src^H dst) for the epilogue.  Ends with the block synchronised.
-// Fused iteration, element j of the last pass: x += alpha p, r -= alpha A p
-// (alpha passed in place of beta); returns |r_j|^2.
-__device__ __forceinline__ double cg_fused_update(const CgArgs& cga, long long j, double2 pv, double2 ap,
-                                                  double alpha) {
-  double2 xv = __ldcg(cga.x + j), rv = __ldcg(cga.rw + j);
-  xv.x += alpha * pv.x;
-  xv.y += alpha * pv.y;
-  rv.x -= alpha * ap.x;
-  rv.y -= alpha * ap.y;
-  cga.x[j] = xv;
-  cga.rw[j] = rv;
-  return rv.x * rv.x + rv.y * rv.y;
-}
-
 template <typename T, int INM, int OUTM, bool CONV>
 __device__ double line_block(const LineGeom& g, long long blk, const void* __restrict__ in_v, void* out_v, int dir,
                              const cplx<T>* __restrict__ tw, const T* __restrict__ what, const CgArgs& cga,
@@ -265,7 +251,6 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
   }
   __syncthreads();
   const float rnb = 1.0f / (float)nb, rL = 1.0f / (float)L, rno = 1.0f / (float)g.n_out;
-  double pre = 0.0;   // fused iteration: this thread's part of the first or product pass's sum
 
   // ---- load (zero-padded to L)
   for (int e = threadIdx.x; e < nb * L; e += blockDim.x) {
@@ -287,7 +272,6 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
         }
         const double dj = cga.Dw[j];
         v = mk<T>((T)(dj * pv.x), (T)(dj * pv.y));
-        if (cga.fused) pre += cga.sigma2 * (pv.x * pv.x + pv.y * pv.y);
       }
     }
     b0[li * LP + k] = v;
@@ -305,7 +289,6 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
       if (bw >= 0) {
         const T wv = __ldg(what + (bw + (long long)k * g.inner));
         cplx<T> t = res[li * LP + k];
-        if (cga.fused) pre += (double)wv * ((double)t.x * t.x + (double)t.y * t.y);
         res[li * LP + k] = mk<T>(t.x * wv, t.y * wv);
       }
     }
@@ -333,17 +316,13 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
       double2 a;
       a.x = dj * (double)v.x + cga.sigma2 * sv.x;
       a.y = dj * (double)v.y + cga.sigma2 * sv.y;
-      if (cga.fused) {
-        dot += cg_fused_update(cga, j, sv, a, cg_beta);
-      } else {
-        cga.dst[j] = a;
-        dot += sv.x * a.x + sv.y * a.y;   // Re(conj(src) * a)
-      }
+      cga.dst[j] = a;
+      dot += sv.x * a.x + sv.y * a.y;   // Re(conj(src) * a)
     }
   }
 
   __syncthreads();
-  return (INM == IN_CG || CONV) && !(OUTM == OUT_CG) ? pre : dot;
+  return dot;
 }
 
 // Line block blk of pass q of a problem descriptor (the CG variants of the

@@ -275,6 +275,9 @@ def config(name: str, n: int | None = None) -> Recipe:
     elif name == "matern2d_table5":  # Table 5 regime: N / sigma^2 = 3e8 fixed, sigma = 1.83 at N = 1e9
         r = Recipe(d=2, n=1_000_000_000, seed=7, noise=TABLE5_SIGMA, fn="plane", omega=(3.0, 4.0),
                    targets="grid", n_targets_1d=1000)
+    elif name == "batch_largest":  # the batch's largest FFT grid: Matern-1/2 l=0.0341, L = 2625
+        r = Recipe(d=2, n=1_000_000, seed=77, noise=0.1115, fn="cosines", n_cos=5, kmax=5.0,
+                   targets="iid", n_targets=10_000)
     else:
         raise KeyError(name)
     if n is not None:
@@ -293,6 +296,7 @@ MODELS = {
     "matern2d_1e9": ("matern", 1.5, 0.05, 0.5, 1e-3),
     "matern2d_table4": ("matern", 1.5, 0.1, 0.1, 1e-5),
     "matern2d_table5": ("matern", 1.5, 0.1, TABLE5_SIGMA, 1e-5),
+    "batch_largest": ("matern", 0.5, 0.0341, 0.1115, 1e-4),
 }
 
 

@@ -4,7 +4,7 @@ configuration (default options, device inputs).
 The oracle cannot form all (4m+1)^2 Toeplitz entries from 1e9 points, so it
 checks what it can compute one by one: sampled entries of w (eq. 88) and
 b = D F^* y (eq. rhs) by direct sums over all 1e9 points; then, from the
-GPU's own (verified) w and b, the dense Cholesky solution and the direct
+GPU's own (verified) w and b, the dense solution (LU) and the direct
 posterior mean at sampled targets, which must match the GPU's CG + type-2
 mean to 10 eps max|y|.
 """
@@ -67,9 +67,14 @@ def test_billion_point_workload_sampled_parity(E):
         j = (k[0] + m) * (2 * m + 1) + (k[1] + m)
         assert abs(b[j] / D[j] - ref) <= 3 * tol * ysum, (k, b[j] / D[j], ref)
 
-    # the solve and the mean at sampled targets, from the GPU's own system
+    # the solve and the mean at sampled targets, from the GPU's own system.
+    # D W D + sigma^2 I is Hermitian positive definite in exact arithmetic
+    # (Sec. 3), but the GPU's w carries NUFFT errors near tol * N per entry
+    # (tolerance eps/10, Sec. 5.1), which at N = 1e9 can leave the assembled
+    # matrix slightly indefinite: the dense solve is LU, with its residual checked
     A = O.system_matrix(w, D, sigma, m, 2)
-    beta = O.solve_weights(A, b)
+    beta = np.linalg.solve(A, b)
+    assert np.linalg.norm(A @ beta - b) <= 1e-6 * np.linalg.norm(b)   # far below the CG tolerance eps/10
     del A
     zs_idx = rng.choice(mu.shape[0], 2000, replace=False)
     zs = synthdata.targets_np(rec)[zs_idx]

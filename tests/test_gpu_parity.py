@@ -441,26 +441,3 @@ def test_many_targets_shared_memory_interpolation(E):
     idx = np.random.default_rng(9).choice(q, 1500, replace=False)
     ref = _oracle((name, 50_000, "smem", 1500), x, y, z[idx].astype(np.float64), ok, sigma, eps)
     assert np.abs(mu_all[idx] - ref.mu).max() <= 10 * eps * np.abs(y).max()
-
-
-@pytest.mark.parametrize("name,n,prec", [("matern2d", 100_000, "mixed"), ("se3d", 50_000, "mixed"),
-                                         ("matern2d", 20_000, "fp64"), ("se3d", 5_000, "fp64")])
-def test_fused_iteration_matches_separate_update(E, name, n, prec):
-    """The graph-launched iteration with p^H A p taken by Parseval in the
-    w-hat product pass and x, r updated by the last pass (cg_fuse 1) against
-    the same passes followed by the separate update kernel (cg_fuse 2)."""
-    rec = synthdata.config(name, n=n)
-    x, y, z = synthdata.make_np(rec)
-    z = z[:5000]
-    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS[name])
-    out = {}
-    for fuse in (1, 2):
-        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, precision=prec, cg_fuse=fuse)
-        info = h.solve()
-        assert info["converged"], (fuse, info)
-        assert info["true_rel_residual"] <= 10 * eps, (fuse, info)
-        out[fuse] = (info, h.predict(_dev(z)).double().cpu().numpy())
-        h.close()
-    (i0, m0), (i2, m2) = out[1], out[2]
-    assert abs(i0["iters"] - i2["iters"]) <= max(5, 0.1 * i2["iters"]), (i0, i2)
-    assert np.abs(m0 - m2).max() <= 0.2 * 10 * eps * np.abs(y).max()
