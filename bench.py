@@ -266,7 +266,7 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
 
     def step():
-        B = E.batch_setup(items, cg_mode=args.cg_mode)
+        B = E.batch_setup(items, precision=args.precision or "mixed", cg_mode=args.cg_mode, autotune=args.autotune)
         infos = B.solve()
         for i in range(len(items)):
             B.predict(i, targets[i])
@@ -293,12 +293,15 @@ def run_batch(args, rank, world):
         print(json.dumps({
             "metric": METRIC, "value": job_throughput(npts, world, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if (args.precision or "mixed") == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": f"batch of {len(items)} 2D Matern-1/2 and 3/2 problems, N log-uniform "
                                    f"[1e4, 1e7] (total {npts}), l U[0.03, 0.3], sigma U[0.1, 1], eps 1e-4, "
                                    "1e4 iid targets each", "problems": len(items), "points": npts},
             "cg_iters_max": max(iters), "cg_iters_median": sorted(iters)[len(iters) // 2],
             "cg_iters_total": sum(iters), "cg_ms": sum(solve_ms) / len(solve_ms), "cg_mode": args.cg_mode,
+            "cg_iters_per_s": sum(iters) / (sum(solve_ms) / len(solve_ms) / 1000),
+            "precision": args.precision or "mixed",
             "clocks": clk.summary(),
         }), flush=True)
     if dist:
@@ -338,7 +341,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
 
     def step(profile=0):
-        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile, cg_mode=args.cg_mode)
+        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile, cg_mode=args.cg_mode,
+                    autotune=args.autotune)
         info = h.solve()
         mu = h.predict(z)
         pt = h.phase_times()
@@ -482,6 +486,7 @@ def run_ours(args, rank, world):
                        "w2": par["w2"], "l2_flush": "inputs larger than L2 (%.1f GB)" % (
                            rec.n * (d * coord_b + val_b) / 1e9), "parallelism": f"independent problem per GPU x{world}"},
             "cg_iters": iters, "cg_rel_residual": [i["rel_residual"] for i in infos],
+            "cg_iters_per_s": (sum(iters) / len(iters)) / (tot["cg_ms"] / 1000) if tot.get("cg_ms") else None,
             "phase_ms": {k.replace("_ms", ""): round(v, 4) for k, v in tot.items()},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu,
@@ -505,6 +510,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--once", action="store_true", help="run one untimed step and exit (profiling target)")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
+                    help="time candidate line batches per Toeplitz pass before the CG graph is captured")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1, 2, 3],
                     help="CG launch form (0 chooses; see efgp_options.cg_mode)")
     ap.add_argument("--at-data", action="store_true",

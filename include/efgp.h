@@ -83,7 +83,9 @@ typedef struct {
   double upsampfac;     /* > 0: NUFFT fine-grid upsampling factor (else chosen)           */
   int es_width;         /* > 0: ES kernel width in grid points (else chosen)              */
   int iters_per_launch; /* CG iterations per captured CUDA graph launch (0: 32)           */
-  int autotune;         /* 1: time candidate FFT line batches once per shape              */
+  int autotune;         /* 1: before the CG graph is captured, time each line pass of the  */
+                        /* product at a few line batches and thread counts (once per pass */
+                        /* shape and precision in the process) and keep the fastest      */
   int profile;          /* 1: time each phase with CUDA events (efgp_get_phase_times)     */
   int cg_mode;          /* 0: choose (one problem: 1; a batch: 3);                      */
                         /* 1: graph-captured kernels per iteration;                        */

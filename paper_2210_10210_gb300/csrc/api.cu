@@ -12,6 +12,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "handle.h"
@@ -657,8 +658,103 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   return EFGP_OK;
 }
 
+// ---- autotuner (efgp_options.autotune): the line batch (lines per block) and
+// thread count of every line pass of the graph-launched product are timed on
+// the device once per pass shape and precision, from the default choice and
+// its halved and doubled batch at 256 and 512 threads; the fastest is kept
+// for the process.
+struct TuneKey {
+  int L, n_in, n_out, elem, inm, outm, conv;
+  long long outer, inner, in_sk, out_sk;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(L, n_in, n_out, elem, inm, outm, conv, outer, inner, in_sk, out_sk) <
+           std::tie(o.L, o.n_in, o.n_out, o.elem, o.inm, o.outm, o.conv, o.outer, o.inner, o.in_sk, o.out_sk);
+  }
+};
+
+int autotune_passes(efgp_handle* H, std::vector<Pass>& ps) {
+  static std::mutex mu;
+  static std::map<TuneKey, std::pair<int, int>> tuned;   // -> (lines per block, threads)
+  CgArgs cga{};
+  cga.src = H->p;
+  cga.r = H->r;
+  cga.Dw = H->Dw;
+  cga.dst = H->Ap;
+  cga.sigma2 = H->sigma * H->sigma;
+  void* bufs[3] = {nullptr, H->scrA, H->scrB};
+  cudaEvent_t e0, e1;
+  EFGP_CK(cudaEventCreate(&e0));
+  EFGP_CK(cudaEventCreate(&e1));
+  int rc = EFGP_OK;
+  for (Pass& p : ps) {
+    if (p.kind != 0) continue;
+    const TuneKey key{p.g.L, p.g.n_in, p.g.n_out, (int)H->elem, p.inm, p.outm, p.conv ? 1 : 0,
+                      p.g.outer, p.g.inner, p.g.in_sk, p.g.out_sk};
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = tuned.find(key);
+      if (it != tuned.end()) {
+        p.g.nb = it->second.first;
+        p.threads = it->second.second;
+        continue;
+      }
+    }
+    std::vector<std::pair<int, int>> cands;
+    for (int nb : {p.g.nb, std::max(1, p.g.nb / 2), std::min(kMaxLineBatch, 2 * p.g.nb)})
+      for (int th : {256, 512})
+        if (line_fft_smem_bytes(p.g.L, nb, H->elem) <= (size_t)kLineFftMaxSmem &&
+            std::find(cands.begin(), cands.end(), std::make_pair(nb, th)) == cands.end())
+          cands.push_back({nb, th});
+    float best = 1e30f;
+    std::pair<int, int> pick{p.g.nb, p.threads};
+    for (const auto& c : cands) {
+      Pass t = p;
+      t.g.nb = c.first;
+      t.threads = c.second;
+      auto launch = [&]() -> cudaError_t {
+        if (H->f64)
+          return launch_line_fft<double>(t.g, bufs[t.in_buf], bufs[t.out_buf], t.dir,
+                                         reinterpret_cast<const double2*>(H->twL),
+                                         t.conv ? reinterpret_cast<const double*>(H->what) : nullptr, t.inm, t.outm,
+                                         &cga, t.threads, H->stream);
+        return launch_line_fft<float>(t.g, bufs[t.in_buf], bufs[t.out_buf], t.dir,
+                                      reinterpret_cast<const float2*>(H->twL),
+                                      t.conv ? reinterpret_cast<const float*>(H->what) : nullptr, t.inm, t.outm, &cga,
+                                      t.threads, H->stream);
+      };
+      cudaError_t e = launch();
+      for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+        if (r == 0) e = cudaEventRecord(e0, H->stream);
+        if (e == cudaSuccess) e = launch();
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, H->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        set_error(std::string("autotune: ") + cudaGetErrorString(e));
+        rc = EFGP_ECUDA;
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    if (rc != EFGP_OK) break;
+    p.g.nb = pick.first;
+    p.threads = pick.second;
+    std::lock_guard<std::mutex> lk(mu);
+    tuned[key] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 int capture_cg_graph(efgp_handle* H) {
   if (H->graph) return EFGP_OK;
+  if (H->opt.autotune) EFGP_TRY(autotune_passes(H, H->mvg));
   const int iters = H->opt.iters_per_launch > 0 ? H->opt.iters_per_launch : 32;
   CgArgs cga{};
   cga.src = H->p;
@@ -982,7 +1078,8 @@ int handle_init(efgp_handle* H, int d, long long N, const efgp_kernel* kern, dou
   long long maxblocks = 1024;
   for (const Pass& p : H->mv) maxblocks = std::max(maxblocks, pass_blocks(p));
   for (const Pass& p : H->mvg) maxblocks = std::max(maxblocks, pass_blocks(p));
-  EFGP_TRY(H->alloc((void**)&H->partials, sizeof(double) * (maxblocks + 16)));
+  // (twice the largest default grid: the autotuner may halve a line batch)
+  EFGP_TRY(H->alloc((void**)&H->partials, sizeof(double) * (2 * maxblocks + 16)));
   EFGP_TRY(H->alloc(&H->scrA, H->elem * scratch));
   EFGP_TRY(H->alloc(&H->scrB, H->elem * scratch));
   EFGP_TRY(H->alloc((void**)&H->flag, sizeof(int) * 4));

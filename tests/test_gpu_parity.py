@@ -441,3 +441,23 @@ def test_many_targets_shared_memory_interpolation(E):
     idx = np.random.default_rng(9).choice(q, 1500, replace=False)
     ref = _oracle((name, 50_000, "smem", 1500), x, y, z[idx].astype(np.float64), ok, sigma, eps)
     assert np.abs(mu_all[idx] - ref.mu).max() <= 10 * eps * np.abs(y).max()
+
+
+@pytest.mark.parametrize("name,n", [("matern2d", 100_000), ("se3d", 50_000)])
+def test_autotuned_passes_match_default(E, name, n):
+    """efgp_options.autotune re-chooses the line batch and thread count of each
+    Toeplitz pass by timing; the solve must agree with the default choice."""
+    rec = synthdata.config(name, n=n)
+    x, y, z = synthdata.make_np(rec)
+    z = z[:5000]
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS[name])
+    out = []
+    for tune in (0, 1):
+        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, autotune=tune)
+        info = h.solve()
+        assert info["converged"] and info["true_rel_residual"] <= 10 * eps, (tune, info)
+        out.append((info, h.predict(_dev(z)).double().cpu().numpy()))
+        h.close()
+    (i0, m0), (i1, m1) = out
+    assert abs(i0["iters"] - i1["iters"]) <= max(5, 0.1 * i0["iters"])
+    assert np.abs(m0 - m1).max() <= 0.2 * 10 * eps * np.abs(y).max()
