@@ -308,6 +308,71 @@ def run_batch(args, rank, world):
         dist.destroy_process_group()
 
 
+def toeplitz_matvec_timing(E, h, par, d, sigma, dev, reps=50):
+    """Per-matvec device time of the library's fused Stockham Toeplitz product
+    (efgp_apply_system_device) beside a cuFFT form of the same product
+    (torch.fft: pad, FFT, w-hat product, inverse FFT, crop, D and sigma^2),
+    FP32 grid, captured in a CUDA graph.  The baseline's D is a stand-in
+    (timing only); its w-hat comes from the handle's Toeplitz vector."""
+    import torch
+    M, L, m = int(par["M"]), int(par["L"]), int(par["m"])
+    n1 = 2 * m + 1
+    g = torch.Generator(device=dev).manual_seed(0)
+    v = torch.randn(M, dtype=torch.complex128, device=dev, generator=g)
+    out = torch.empty_like(v)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        h.apply_system_device(v, out)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        h.apply_system_device(v, out)
+    ev1.record()
+    torch.cuda.synchronize()
+    ours = ev0.elapsed_time(ev1) * 1000 / reps
+
+    w, _ = h.system()
+    wt = torch.from_numpy(w).to(dev)
+    ks = torch.arange(-2 * m, 2 * m + 1, device=dev) % L
+    grid = torch.zeros((L,) * d, dtype=torch.complex128, device=dev)
+    grid[torch.meshgrid(*([ks] * d), indexing="ij")] = wt
+    what = (torch.fft.fftn(grid).real / L ** d).float()
+    del grid
+    Dv = torch.rand(M, dtype=torch.float64, device=dev, generator=g) + 0.5
+    buf = torch.zeros((L,) * d, dtype=torch.complex64, device=dev)
+    crop = (slice(0, n1),) * d
+    s2 = sigma * sigma
+
+    def matvec():
+        buf.zero_()
+        buf[crop] = (Dv * v).to(torch.complex64).reshape((n1,) * d)
+        U = torch.fft.fftn(buf)
+        U *= what
+        y = torch.fft.ifftn(U, norm="forward")
+        return Dv * y[crop].reshape(-1).to(torch.complex128) + s2 * v
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            matvec()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        matvec()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        graph.replay()
+    ev1.record()
+    torch.cuda.synchronize()
+    cufft = ev0.elapsed_time(ev1) * 1000 / reps
+    return {"L": L, "grid": f"{L}^{d}", "ours_us": ours, "cufft_graph_us": cufft,
+            "note": "per product A v; cuFFT form via torch.fft in a CUDA graph, FP32 grid, stand-in D"}
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2210_10210_gb300 as E
@@ -412,6 +477,13 @@ def run_ours(args, rank, world):
                 "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                 "peak_source": src, "alg_bytes_per_launch": alg[roof_kernel], "ms_per_launch": kt}
 
+    # the Toeplitz product beside a cuFFT form of it
+    matvec = None
+    if not args.no_fft_baseline:
+        hm = E.setup(x, y, kern, sigma, eps, precision=prec)
+        matvec = toeplitz_matvec_timing(E, hm, hm.params(), d, sigma, dev)
+        hm.close()
+
     # posterior mean at all N training points (type-2 with q = N)
     at_data = None
     if args.at_data:
@@ -493,6 +565,8 @@ def run_ours(args, rank, world):
         }
         if at_data:
             line["mean_at_data"] = at_data
+        if matvec:
+            line["toeplitz_matvec"] = matvec
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -510,6 +584,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--once", action="store_true", help="run one untimed step and exit (profiling target)")
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--no-fft-baseline", action="store_true",
+                    help="skip timing the Toeplitz product beside its cuFFT form")
     ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
                     help="time candidate line batches per Toeplitz pass before the CG graph is captured")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1, 2, 3],

@@ -223,6 +223,13 @@ int efgp_get_system(const efgp_handle* h, double* w_host, double* b_host);
  * complex float64 in host memory (a test accessor for the Toeplitz matvec). */
 int efgp_apply_system(efgp_handle* h, const double* in_host, double* out_host);
 
+/* The same product on device arrays (M complex float64 each, interleaved),
+ * enqueued on the handle's stream without synchronising (for timing the
+ * Toeplitz matvec, Algorithm 1 steps 3-6, in place).  in and out must not
+ * overlap; the handle's FFT scratch is used, so calls on one handle must not
+ * run concurrently with its solve. */
+int efgp_apply_system_device(efgp_handle* h, const void* in_dev, void* out_dev);
+
 /* ---- batched problems: one CG launch sequence for many problems ---------- */
 
 typedef struct {

@@ -216,6 +216,12 @@ class Handle:
         _check(_capi.lib().efgp_get_system(self._p, w.ctypes.data, b.ctypes.data), "efgp_get_system")
         return w.view(np.complex128).reshape((4 * p["m"] + 1,) * self.d), b.view(np.complex128)
 
+    def apply_system_device(self, v, out):
+        """out = A v on the device (complex128 CUDA tensors of M entries), stream-ordered."""
+        assert v.dtype == out.dtype and v.is_contiguous() and out.is_contiguous()
+        _check(_capi.lib().efgp_apply_system_device(self._p, v.data_ptr(), out.data_ptr()),
+               "efgp_apply_system_device")
+
     def apply_system(self, v) -> np.ndarray:
         v = np.ascontiguousarray(v, dtype=np.complex128)
         out = np.empty_like(v)

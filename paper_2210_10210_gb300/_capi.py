@@ -78,6 +78,7 @@ SIGNATURES = [
     ("efgp_get_phase_times", C.c_int, [C.c_void_p, C.POINTER(efgp_phase_times)]),
     ("efgp_get_system", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("efgp_set_beta", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("efgp_apply_system_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("efgp_apply_system", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("efgp_batch_setup", C.c_int, [C.POINTER(efgp_problem), C.c_int, C.POINTER(efgp_options),
                                    C.POINTER(C.c_void_p), C.POINTER(C.c_int)]),

@@ -1414,6 +1414,12 @@ int efgp_apply_system(efgp_handle* H, const double* in_host, double* out_host) {
   return EFGP_OK;
 }
 
+int efgp_apply_system_device(efgp_handle* H, const void* in_dev, void* out_dev) {
+  if (!H || !in_dev || !out_dev || in_dev == out_dev) return EFGP_EINVAL;
+  return apply_system_dev(H, const_cast<double2*>(reinterpret_cast<const double2*>(in_dev)),
+                          reinterpret_cast<double2*>(out_dev));
+}
+
 // ---------------------------------------------------------------------------
 // Batches
 // ---------------------------------------------------------------------------

@@ -461,3 +461,22 @@ def test_autotuned_passes_match_default(E, name, n):
     (i0, m0), (i1, m1) = out
     assert abs(i0["iters"] - i1["iters"]) <= max(5, 0.1 * i0["iters"])
     assert np.abs(m0 - m1).max() <= 0.2 * 10 * eps * np.abs(y).max()
+
+
+def test_device_apply_matches_host_apply(E):
+    """efgp_apply_system_device (device arrays, stream-ordered) gives the same
+    product as the host-pointer accessor."""
+    rec = synthdata.config("matern2d", n=20_000)
+    x, y, _ = synthdata.make_np(rec)
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
+    h = E.setup(_dev(x), _dev(y), ek, sigma, eps)
+    M = h.params()["M"]
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    want = h.apply_system(v)
+    vd = torch.from_numpy(v).cuda()
+    out = torch.empty_like(vd)
+    h.apply_system_device(vd, out)
+    torch.cuda.synchronize()
+    h.close()
+    assert np.array_equal(out.cpu().numpy(), want)
