@@ -187,6 +187,27 @@ def oracle_sample(name, n_sample, q_sample):
     return n_sample / dt, dt
 
 
+def cpu_efgp_sample(name, n_sample, q_sample):
+    """The multithreaded FP64 CPU EFGP (ES-kernel NUFFTs, FFT Toeplitz CG,
+    scipy.fft on all host cores) on the first n_sample points and q_sample
+    targets of the workload."""
+    from oracle import cpu_efgp as C
+    from oracle import efgp_oracle as O
+    rec = synthdata.config(name, n=n_sample)
+    x, y, z = synthdata.make_np(rec)
+    z = z[:q_sample]
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    t0 = time.perf_counter()
+    _, info = C.efgp(x, y, z, O.Kernel(fam, nu, ell), sigma, eps)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt, info
+
+
+def cpu_efgp_sample_size(name):
+    return {"se1d": 10_000, "matern2d": 1_000_000, "se3d": 1_000_000, "matern2d_1e9": 10_000_000,
+            "matern2d_table4": 2_000_000, "matern2d_table5": 2_000_000}.get(name, 1_000_000)
+
+
 def cpu_sample_size(name):
     return {"se1d": 10_000, "matern2d": 200_000, "se3d": 20_000, "matern2d_1e9": 500_000,
             "matern2d_table4": 50_000, "matern2d_table5": 50_000}.get(name, 100_000)
@@ -540,12 +561,17 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes + zn.nbytes), "d2h_bytes_per_step": int(mu_h.nbytes),
                "ms_per_step": 1000 * te}
 
-    cpu = None
+    cpu = cpu_efgp = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ns = cpu_sample_size(name)
         v, dt = oracle_sample(name, ns, 10_000)
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"first {ns} points of the workload, 10000 targets, same h and m ({dt:.1f} s)"}
+        ne = cpu_efgp_sample_size(name)
+        ve, dte, inf = cpu_efgp_sample(name, ne, 10_000)
+        cpu_efgp = {"value": ve, "unit": UNIT, "cores": os.cpu_count(), "kind": "cpu_efgp",
+                    "sample": f"first {ne} points of the workload, 10000 targets, same h and m, "
+                              f"{inf['iters']} CG iterations ({dte:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -567,6 +593,8 @@ def run_ours(args, rank, world):
             line["mean_at_data"] = at_data
         if matvec:
             line["toeplitz_matvec"] = matvec
+        if cpu_efgp:
+            line["cpu_efgp"] = cpu_efgp
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
