@@ -24,7 +24,7 @@
  *  - The library never frees or retains caller memory: it copies what it
  *    needs into its own workspace.  Caller buffers may be reused once the
  *    call has returned (all calls synchronise the handle's stream before
- *    returning, except efgp_setup with host_io = 0 which only orders its work
+ *    returning, except efgp_apply_system_device, which only orders its work
  *    on that stream).
  *  - Frequency multi-indices j in {-m..m}^d are stored row-major with the
  *    first coordinate slowest: j sits at flat index sum_l (j_l+m)(2m+1)^(d-1-l).
@@ -250,10 +250,15 @@ typedef struct efgp_batch efgp_batch;
 int efgp_batch_setup(const efgp_problem* probs, int nprob, const efgp_options* opt,
                      efgp_batch** out, int* failed_index);
 
-/* Solve all problems: every CG iteration of every unconverged problem runs in
- * the same kernel launches (one captured CUDA graph per group of iterations);
- * each problem stops at its own tolerance.  info: nprob entries or NULL.
- * Returns ENOTCONV if any problem hit its cap. */
+/* Solve all problems (step 4 for each), each to its own tolerance.  By
+ * default (cg_mode 0 or 3) one launch of a work-claiming scheduler runs every
+ * problem's CG: resident blocks claim work items (FFT line batches, vector
+ * chunks) of any problem's current phase, and the block finishing a phase
+ * reduces it and publishes the next; its device-side waits for work are
+ * bounded (ETIMEOUT).  cg_mode 1 captures a CUDA graph per group of
+ * iterations with a branch per problem; cg_mode 2 runs one thread-block
+ * cluster per problem.  info: nprob entries or NULL (true_rel_residual is
+ * -1: not recomputed).  Returns ENOTCONV if any problem hit its cap. */
 int efgp_batch_solve(efgp_batch* b, efgp_solve_info* info);
 
 /* Predict problem `index` of the batch at q targets. */
