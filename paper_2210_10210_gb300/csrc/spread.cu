@@ -796,6 +796,7 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
 constexpr int kTmaSpreadThreads = 512;
 constexpr int kTmaSpreadBatch = 8192;
 constexpr int kTmaSpreadSlot = kTmaSpreadBatch + 8;   // floats per staged array
+constexpr int kSpreadUnroll = 2;   // points of a cell whose weights are evaluated together (4: no gain)
 
 template <int D, int W>
 __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
@@ -979,21 +980,17 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
       idx[pos] = (unsigned short)k;
     }
     __syncthreads();
-    // run of my cell: start = cur[cell] - cnt[cell] after the index pass
+    // run of my cell: start = cur[cell] - cnt[cell] after the index pass;
+    // points taken two at a time (independent weight evaluations interleave)
     {
       const int c_n = cnt[cell];
       const int c_s = cur[cell] - c_n;
-      for (int j = half; j < c_n; j += 2) {
-        const int k = idx[c_s + j];
-        float w0[W], w1[W];
-        es_weights_x2<W>(sq0[k] - (float)own[0], cf, w0);
-        const float yv = sy[k];
+      auto add_point = [&](const float (&w0)[W], const float (&w1)[W], float yv) {
         const float2 c2 = make_float2(1.f, yv);
         if (D == 1) {
 #pragma unroll
           for (int u = 0; u < W; ++u) acc[u] = __ffma2_rn(make_float2(w0[u], w0[u]), c2, acc[u]);
         } else {
-          es_weights_x2<W>(sq1[k] - (float)own[D - 1], cf, w1);
 #pragma unroll
           for (int u = 0; u < W; ++u) {
             const float2 wa = __fmul2_rn(make_float2(w0[u], w0[u]), c2);
@@ -1001,6 +998,27 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
             for (int v = 0; v < W; ++v) acc[u * W + v] = __ffma2_rn(wa, make_float2(w1[v], w1[v]), acc[u * W + v]);
           }
         }
+      };
+      constexpr int UP = kSpreadUnroll;
+      int j = half;
+      for (; j + 2 * (UP - 1) < c_n; j += 2 * UP) {
+        int kk[UP];
+        float w0[UP][W], w1[UP][W];
+#pragma unroll
+        for (int e = 0; e < UP; ++e) {
+          kk[e] = idx[c_s + j + 2 * e];
+          es_weights_x2<W>(sq0[kk[e]] - (float)own[0], cf, w0[e]);
+          if (D == 2) es_weights_x2<W>(sq1[kk[e]] - (float)own[D - 1], cf, w1[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < UP; ++e) add_point(w0[e], w1[e], sy[kk[e]]);
+      }
+      for (; j < c_n; j += 2) {
+        const int k = idx[c_s + j];
+        float w0[W], w1[W];
+        es_weights_x2<W>(sq0[k] - (float)own[0], cf, w0);
+        if (D == 2) es_weights_x2<W>(sq1[k] - (float)own[D - 1], cf, w1);
+        add_point(w0, w1, sy[k]);
       }
     }
     __syncthreads();
