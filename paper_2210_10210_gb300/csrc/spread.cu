@@ -817,6 +817,7 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
   unsigned short* idx = reinterpret_cast<unsigned short*>(tile + 2 * CELLS);  // B
   int* cnt = reinterpret_cast<int*>(idx + B);                      // 256
   int* cur = cnt + 256;                                            // 256
+  unsigned char* ucell = reinterpret_cast<unsigned char*>(cur + 256);   // B: each point's cell
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int wtot[8];
   __shared__ int it_tile[2], it_off[2];
@@ -933,12 +934,14 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
     const float* sq0 = stage + (b * NA) * SLOT + off;
     const float* sq1 = stage + (b * NA + (D - 1)) * SLOT + off;
     const float* sy = stage + (b * NA + D) * SLOT + off;
-    // count by cell
+    // count by cell (the cell is kept for the index pass)
     for (int k = t; k < n; k += NT) {
       float q[D], f[D];
       q[0] = sq0[k];
       if (D == 2) q[D - 1] = sq1[k];
-      atomicAdd(&cnt[reg_cell<D>(q, f)], 1);
+      const int c = reg_cell<D>(q, f);
+      ucell[k] = (unsigned char)c;
+      atomicAdd(&cnt[c], 1);
     }
     __syncthreads();
     int mine = 0, st = 0;
@@ -973,10 +976,7 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
     }
     __syncthreads();
     for (int k = t; k < n; k += NT) {
-      float q[D], f[D];
-      q[0] = sq0[k];
-      if (D == 2) q[D - 1] = sq1[k];
-      const int pos = atomicAdd(&cur[reg_cell<D>(q, f)], 1);
+      const int pos = atomicAdd(&cur[ucell[k]], 1);
       idx[pos] = (unsigned short)k;
     }
     __syncthreads();
@@ -1082,7 +1082,7 @@ size_t spread_tma_smem(int d, int W) {
   const int S = TB + W - 1;
   const int cells = d == 1 ? S : S * S;
   return sizeof(float) * (2 * (size_t)(d + 1) * kTmaSpreadSlot + 2 * cells) +
-         sizeof(unsigned short) * kTmaSpreadBatch + sizeof(int) * 512;
+         sizeof(unsigned short) * kTmaSpreadBatch + sizeof(int) * 512 + sizeof(unsigned char) * kTmaSpreadBatch;
 }
 
 size_t spread_reg_smem(int d, int W) {
