@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kSortThreads) bin_scatter_kernel(const TC* __r
                                                                    int soa, long long N, SortGeom sg,
                                                                    long long* __restrict__ cursor,
                                                                    TR* __restrict__ rec) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   const bool sm = sg.ntiles <= kSmemBins;
   long long* base = reinterpret_cast<long long*>(smraw);
   unsigned int* hist = reinterpret_cast<unsigned int*>(base + (sm ? sg.ntiles : 0));
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256) bin_scatter_sorted_kernel(const TC* __res
                                                                  long long* __restrict__ cursor,
                                                                  TR* __restrict__ rec) {
   constexpr int P = 256 * PPT;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int T = sg.ntiles;
   TR* sq = reinterpret_cast<TR*>(smraw);                                   // (D+1) x P
   long long* base = reinterpret_cast<long long*>(sq + (size_t)(D + 1) * P);  // T
@@ -472,7 +472,7 @@ template <int D, int W, typename TR>
 __global__ void __launch_bounds__(256) spread_kernel(const TR* __restrict__ rec, long long N, SortGeom sg,
                                                      const long long* __restrict__ tile_off, long long seg_len,
                                                      EsCoef<TR> cf, double2* __restrict__ E) {
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   TR* acc = reinterpret_cast<TR*>(smraw);
   __shared__ int t_first;
   const int TB = sg.TB;
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
   constexpr int S = TB + W - 1;
   constexpr int CELLS = (D == 1) ? S : S * S;
   constexpr int FP = (D == 1) ? W : W * W;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   float* sf = reinterpret_cast<float*>(smraw);            // D x kRegBatchPad fractional offsets
   float* sy = sf + D * kRegBatchPad;                        // kRegBatchPad values
   float* tile = sy + kRegBatchPad;                          // 2*CELLS
@@ -1111,23 +1111,23 @@ __global__ void fold_kernel(const double2* __restrict__ E, int nEx, int off, int
     for (int a = 0; a < D; ++a) e0[a] = (p[a] + off) % nf;
     double sx = 0.0, sy = 0.0;
     for (int i0 = e0[0]; i0 < nEx; i0 += nf) {
-      if (D == 1) {
+      if constexpr (D == 1) {
         const double2 v = E[i0];
         sx += v.x;
         sy += v.y;
-        continue;
-      }
-      for (int i1 = e0[1 % D]; i1 < nEx; i1 += nf) {
-        if (D == 2) {
-          const double2 v = E[(long long)i0 * nEx + i1];
-          sx += v.x;
-          sy += v.y;
-          continue;
-        }
-        for (int i2 = e0[D - 1]; i2 < nEx; i2 += nf) {
-          const double2 v = E[((long long)i0 * nEx + i1) * nEx + i2];
-          sx += v.x;
-          sy += v.y;
+      } else {
+        for (int i1 = e0[1 % D]; i1 < nEx; i1 += nf) {
+          if constexpr (D == 2) {
+            const double2 v = E[(long long)i0 * nEx + i1];
+            sx += v.x;
+            sy += v.y;
+          } else {
+            for (int i2 = e0[D - 1]; i2 < nEx; i2 += nf) {
+              const double2 v = E[((long long)i0 * nEx + i1) * nEx + i2];
+              sx += v.x;
+              sy += v.y;
+            }
+          }
         }
       }
     }
