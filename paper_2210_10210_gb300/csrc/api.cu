@@ -277,6 +277,22 @@ double default_rho(double eps) { return eps / 10.0; }
 // ---------------------------------------------------------------------------
 namespace {
 
+// Two timing events, destroyed when the scope ends (early error returns included).
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    return e != cudaSuccess ? e : cudaEventCreate(&b);
+  }
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
 // Blocks of a pass's launch.
 long long pass_blocks(const Pass& p) { return p.kind ? p.n1 : (p.g.outer * p.g.inner + p.g.nb - 1) / p.g.nb; }
 
@@ -682,9 +698,9 @@ int autotune_passes(efgp_handle* H, std::vector<Pass>& ps) {
   cga.dst = H->Ap;
   cga.sigma2 = H->sigma * H->sigma;
   void* bufs[3] = {nullptr, H->scrA, H->scrB};
-  cudaEvent_t e0, e1;
-  EFGP_CK(cudaEventCreate(&e0));
-  EFGP_CK(cudaEventCreate(&e1));
+  EventPair evp;   // destroyed on every return path
+  EFGP_CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   int rc = EFGP_OK;
   for (Pass& p : ps) {
     if (p.kind != 0) continue;
@@ -747,8 +763,6 @@ int autotune_passes(efgp_handle* H, std::vector<Pass>& ps) {
     std::lock_guard<std::mutex> lk(mu);
     tuned[key] = pick;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return rc;
 }
 
@@ -970,9 +984,9 @@ int run_queue(const std::vector<efgp_handle*>& hs, const std::vector<QueueProble
       EFGP_CK(cudaMemcpyAsync(&qs[i].ctl->word, &kStalledWord, sizeof(kStalledWord), cudaMemcpyHostToDevice, s));
   }
   EFGP_CK(cudaMemcpyAsync(d_probs, qs.data(), sizeof(QueueProblem) * n, cudaMemcpyHostToDevice, s));
-  cudaEvent_t e0, e1;
-  EFGP_CK(cudaEventCreate(&e0));
-  EFGP_CK(cudaEventCreate(&e1));
+  EventPair evp;   // destroyed on every return path
+  EFGP_CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   EFGP_CK(cudaEventRecord(e0, s));
   EFGP_CK(launch_cg_queue(d_probs, n, aux, f64, smem, blocks, idle_limit, s));
   EFGP_CK(cudaEventRecord(e1, s));
@@ -983,8 +997,6 @@ int run_queue(const std::vector<efgp_handle*>& hs, const std::vector<QueueProble
   EFGP_CK(cudaStreamSynchronize(s));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   *ms_out = ms;
   for (efgp_handle* H : hs) H->times.launches += 1;
   if (haux[1] != 0 || haux[0] != (unsigned)n) {
@@ -1217,9 +1229,9 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
     if (!H->qaux) EFGP_TRY(H->alloc((void**)&H->qaux, 4 * sizeof(unsigned int)));
     EFGP_TRY(run_queue({H}, qs, smem, H->d_qprob, H->qaux, H->host_state, H->stream, &qms));
   }
-  cudaEvent_t e0, e1;
-  EFGP_CK(cudaEventCreate(&e0));
-  EFGP_CK(cudaEventCreate(&e1));
+  EventPair evp;   // destroyed on every return path
+  EFGP_CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   EFGP_CK(cudaEventRecord(e0, H->stream));
   if (queued) {
   } else if (persistent) {
@@ -1257,8 +1269,6 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   if (queued) ms = qms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   H->solved = true;
   H->times.cg_ms += ms;
   H->times.n_solve += 1;
@@ -1565,9 +1575,9 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
       for (efgp_handle* H : B->hs) EFGP_CK(cudaStreamSynchronize(H->stream));
       EFGP_CK(cudaMemcpyAsync(B->d_probs, B->h_probs.data(), sizeof(PersistentProblem) * n, cudaMemcpyHostToDevice,
                               B->main));
-      cudaEvent_t e0, e1;
-      EFGP_CK(cudaEventCreate(&e0));
-      EFGP_CK(cudaEventCreate(&e1));
+      EventPair evp;   // destroyed on every return path
+      EFGP_CK(evp.create());
+      cudaEvent_t e0 = evp.a, e1 = evp.b;
       EFGP_CK(cudaEventRecord(e0, B->main));
       EFGP_CK(launch_cg_persistent(B->d_probs, n, cl, smem, f64, B->main));
       EFGP_CK(cudaEventRecord(e1, B->main));
@@ -1576,8 +1586,6 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
       EFGP_CK(cudaStreamSynchronize(B->main));
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
       int rc = EFGP_OK;
       for (int i = 0; i < n; ++i) {
         efgp_handle* H = B->hs[i];
@@ -1640,9 +1648,9 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
     EFGP_CK(ie);
     B->graph_iters = iters;
   }
-  cudaEvent_t e0, e1;
-  EFGP_CK(cudaEventCreate(&e0));
-  EFGP_CK(cudaEventCreate(&e1));
+  EventPair evp;   // destroyed on every return path
+  EFGP_CK(evp.create());
+  cudaEvent_t e0 = evp.a, e1 = evp.b;
   EFGP_CK(cudaEventRecord(e0, B->main));
   for (efgp_handle* H : B->hs) {
     const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
@@ -1668,8 +1676,6 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
   EFGP_CK(cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   int rc = EFGP_OK;
   for (int i = 0; i < n; ++i) {
     efgp_handle* H = B->hs[i];
