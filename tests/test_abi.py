@@ -135,3 +135,38 @@ def test_nufft_error_estimate_is_conservative():
         p = E.plan(d, 10_000, E.Kernel(fam, nu, ell), 0.3, eps)
         assert p["es_err1"] < eps / 10
         assert p["w1"] >= 3 and p["poly_deg1"] >= p["w1"] - 1
+
+
+def test_ctypes_struct_layouts_match_the_header():
+    """Every struct the binding passes through the C ABI has the same size and
+    field offsets in ctypes as in include/efgp.h (compiled here with gcc)."""
+    import shutil
+    import subprocess
+    import ctypes
+    from paper_2210_10210_gb300 import _capi
+    from paper_2210_10210_gb300 import build as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [_capi.efgp_kernel, _capi.efgp_options, _capi.efgp_params, _capi.efgp_solve_info,
+               _capi.efgp_phase_times, _capi.efgp_problem]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "efgp.h"', 'int main(void) {']
+    for st in structs:
+        n = st.__name__
+        lines.append(f'  printf("{n} sizeof %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ['  return 0;', '}']
+    os.makedirs(B.OUT_DIR, exist_ok=True)   # the package's (ignored) build directory
+    src = os.path.join(B.OUT_DIR, "layout_check.c")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    exe = os.path.join(B.OUT_DIR, "layout_check")
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "sizeof")] == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert got[(n, f)] == getattr(st, f).offset, (n, f)
