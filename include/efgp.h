@@ -51,7 +51,7 @@ typedef enum {
   EFGP_ETIMEOUT = 5,  /* a bounded device-side wait ran out                            */
   EFGP_ECUDA = 6,     /* a CUDA runtime call failed (message: efgp_last_error())       */
   EFGP_ESTATE = 7,    /* call out of order (e.g. predict before solve)                 */
-  EFGP_EUNSUPPORTED = 8 /* a size or option this build does not support                 */
+  EFGP_EUNSUPPORTED = 8 /* a size or option the library does not support                */
 } efgp_status;
 
 typedef enum { EFGP_KERNEL_SE = 0, EFGP_KERNEL_MATERN = 1 } efgp_kernel_family;

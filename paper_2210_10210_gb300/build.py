@@ -1,7 +1,7 @@
 """Builds libefgp.so (the CUDA library behind include/efgp.h) in-tree.
 
 Every translation unit is compiled for sm_103a only, in parallel, and linked
-with the static CUDA runtime so the library depends on nothing but the driver.
+with the static CUDA runtime so the library depends on nothing but the NVIDIA driver.
 Run ``python -m paper_2210_10210_gb300.build`` or call :func:`build`.
 """
 from __future__ import annotations

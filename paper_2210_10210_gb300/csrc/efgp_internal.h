@@ -14,7 +14,7 @@
 namespace efgp {
 
 // ---------------------------------------------------------------------------
-// Limits of this build.
+// Compile-time limits of the library.
 // ---------------------------------------------------------------------------
 constexpr int kMaxWidth = 16;   // largest ES kernel width (grid points per dim)
 constexpr int kMaxDeg = 20;     // largest degree of the piecewise ES polynomial

@@ -252,7 +252,7 @@ def make_torch(rec: Recipe, device, chunk: int = 1 << 26):
     return x, y
 
 
-# ------------------------------------------------- the workloads (SURVEY configs)
+# ------------------------------------------------- named workloads
 def config(name: str, n: int | None = None) -> Recipe:
     """Named workloads.  ``n`` overrides the point count (N-reduced twins)."""
     if name == "se1d":          # 1D SE, l=0.1, sigma=0.3, eps=1e-6, N=1e4, float64
