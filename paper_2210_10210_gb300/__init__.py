@@ -23,7 +23,7 @@ import numpy as np
 from . import _capi
 from ._capi import efgp_kernel, efgp_options, efgp_params, efgp_problem, efgp_solve_info
 
-__all__ = ["Kernel", "EfgpError", "plan", "setup", "Handle", "batch_setup", "Batch", "version"]
+__all__ = ["Kernel", "EfgpError", "plan", "setup", "Handle", "batch_setup", "Batch", "prior_weights", "version"]
 
 
 class EfgpError(RuntimeError):
