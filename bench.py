@@ -191,7 +191,7 @@ def cpu_efgp_sample(name, n_sample, q_sample):
     """The multithreaded FP64 CPU EFGP (ES-kernel NUFFTs, FFT Toeplitz CG,
     scipy.fft on all host cores) on the first n_sample points and q_sample
     targets of the workload."""
-    from oracle import cpu_efgp as C
+    import cpu_efgp as C
     from oracle import efgp_oracle as O
     rec = synthdata.config(name, n=n_sample)
     x, y, z = synthdata.make_np(rec)

@@ -1,10 +1,11 @@
 """Multithreaded FP64 CPU EFGP: the CPU baseline the GPU path is timed beside.
 
 TEST AND BENCHMARK INFRASTRUCTURE, NOT PART OF THE LIBRARY.  Only the test
-suite and the CPU-baseline leg of ``bench.py`` may import this module.  It is
-not the oracle (``efgp_oracle``, which uses direct sums and a dense solve): it
-runs the method the fast way, on the host, in float64, from the same plain
-definitions, and is pinned against the oracle in ``tests/test_cpu_efgp.py``.
+suite and the CPU-baseline leg of ``bench.py`` may import this package.  It is
+not the oracle (``oracle.efgp_oracle``, which uses direct sums and a dense
+solve): it runs the method the fast way, on the host, in float64, from the
+same plain definitions (it takes (h, m) and D from the oracle's parameter
+functions), and is pinned against the oracle in ``tests/test_cpu_efgp.py``.
 
 Steps (Algorithm 2 of the paper, with the nonuniform FFTs of Sec. 4.1):
 
@@ -32,7 +33,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 import scipy.fft as sfft
 
-from . import efgp_oracle as O
+from oracle import efgp_oracle as O
 
 WORKERS = os.cpu_count() or 1
 

@@ -177,22 +177,23 @@ int efgp_solve(efgp_handle* h, efgp_solve_info* info);
 int efgp_predict(efgp_handle* h, const void* targets, int64_t q, void* mu_out);
 
 /* Allocation-free form of efgp_predict, for callers that cannot allocate
- * device memory when they predict: work being recorded into a CUDA stream
- * capture (allocation calls are not capturable), real-time serving loops that
- * must not block in an allocator, and host applications that reserve all
- * device memory up front.  The paper has no counterpart: it is an interface
- * convenience.  Arguments and results are those of efgp_predict, with device
- * pointers only (a handle set up with host_io = 1 gives EFGP_EINVAL).  The two
- * type-2 scratch grids live in one fixed 16 MiB device array inside the
- * library instead of handle memory; a problem whose grids need more (fine
- * grid nf2^d complex plus extended grid nE2^d real, see efgp_get_params)
- * gives EFGP_EUNSUPPORTED with the sizes in efgp_last_error().  The first
- * call on each device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
- * All calls share the one array, which keeps the previous call's contents
- * (the part that must start at zero is cleared by every call), so calls whose
- * work overlaps on the GPU (different streams or threads) race: order them.
- * No cudaMalloc, cudaFree or other allocating call is made. */
+ * device memory when they predict: real-time serving loops that must not
+ * block in an allocator, and host applications that reserve all device memory
+ * up front and forbid plug-ins from allocating.  The paper has no
+ * counterpart: it is an interface convenience.  Arguments and results are
+ * those of efgp_predict, with device pointers only (a handle set up with
+ * host_io = 1 gives EFGP_EINVAL).  The two type-2 scratch grids live in one
+ * fixed 16 MiB device array inside the library instead of handle memory; a
+ * problem whose grids need more (fine grid nf2^d complex plus extended grid
+ * nE2^d real, see efgp_get_params) gives EFGP_EUNSUPPORTED with the sizes in
+ * efgp_last_error().  The first call on each device looks up the array's
+ * device address (once per device, with that device current).  Like
+ * efgp_predict, the call ends by copying the target range flag to the host
+ * and synchronising the handle's stream, so it returns only when mu_out is
+ * written.  All calls share the one array, which keeps the previous call's
+ * contents (the part that must start at zero is cleared by every call), so
+ * calls whose work overlaps on the GPU (different streams or threads) race:
+ * order them.  No cudaMalloc, cudaFree or other allocating call is made. */
 int efgp_predict_noalloc(efgp_handle* h, const void* targets, int64_t q, void* mu_out);
 
 /* Release everything the handle owns.  NULL is ignored. */

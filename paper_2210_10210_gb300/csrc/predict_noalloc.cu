@@ -1,14 +1,13 @@
 // efgp_predict_noalloc: the posterior mean at targets without allocating.
 //
 // Some callers cannot allocate device memory at the point where they need
-// predictions: code that records work into a CUDA stream capture (allocation
-// calls are not capturable and would break the capture), real-time serving
-// loops that must not block in the allocator, and host applications that
-// reserve all device memory up front and forbid plug-ins from allocating.
-// This entry point serves them: it runs the same type-2 steps as
-// efgp_predict, but its two scratch grids live in one statically sized
-// device array defined in this file instead of handle memory allocated on
-// first use.
+// predictions: real-time serving loops that must not block in the allocator,
+// and host applications that reserve all device memory up front and forbid
+// plug-ins from allocating.  This entry point serves them: it runs the same
+// type-2 steps as efgp_predict, but its two scratch grids live in one
+// statically sized device array defined in this file instead of handle
+// memory allocated on first use.  Like efgp_predict it ends with a read-back
+// of the target range flag and a synchronisation of the handle's stream.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import synthdata
-from oracle import cpu_efgp as C
+import cpu_efgp as C
 from oracle import efgp_oracle as O
 
 

@@ -1,8 +1,9 @@
 """The allocation-free prediction entry point, called through the C ABI.
 
 efgp_predict_noalloc serves callers that cannot allocate device memory when
-they predict (stream capture, real-time loops, hosts that reserve all device
-memory); it keeps its scratch grids in a fixed array inside the library.
+they predict (real-time loops that must not block in an allocator, hosts that
+reserve all device memory up front); it keeps its scratch grids in a fixed
+array inside the library.
 This file is collected last so that a failure here does not hide the result
 of any other test.
 """
