@@ -34,17 +34,18 @@ METRIC = "points/s end-to-end EFGP at stated mean error; spread/interp GB/s vs H
 UNIT = "points/s"
 
 
-KERNEL_SRC = os.path.join(ROOT, "paper_2210_10210_gb300", "csrc", "spread.cu")
-KERNEL_NAMES = {"spread": "spread_tma_kernel(", "bin_scatter": "bin_scatter_tma_kernel(",
-                "bin_count": "bin_count_kernel("}
+CSRC = os.path.join(ROOT, "paper_2210_10210_gb300", "csrc")
+KERNEL_NAMES = {"spread": ("spread.cu", "spread_tma_kernel("), "bin_scatter": ("spread.cu", "bin_scatter_tma_kernel("),
+                "bin_count": ("setup_fused.cu", "fused_count_kernel(")}
 
 
 def kernel_fingerprint(key):
-    """SHA-1 of one kernel's source text (template header to closing brace);
-    DRAM counters recorded for another fingerprint are stale."""
-    text = open(KERNEL_SRC).read()
-    i = text.index(KERNEL_NAMES[key])
-    start = text.rfind("template", 0, i)
+    """SHA-1 of one kernel's source text (template header or qualifiers to the
+    closing brace); DRAM counters recorded for another fingerprint are stale."""
+    fname, marker = KERNEL_NAMES[key]
+    text = open(os.path.join(CSRC, fname)).read()
+    i = text.index(marker)
+    start = text.rfind("\n\n", 0, i) + 2
     depth, j = 0, text.index("{", i)
     while j < len(text):
         if text[j] == "{":
@@ -230,6 +231,130 @@ def paper_ratio(name, n, value):
     if name in PAPER_TOTAL_S and n == synthdata.config(name).n:
         return value / (n / PAPER_TOTAL_S[name])
     return None
+
+
+def setup_roofline(rec, d, coord_b, val_b, rec_bytes, tot, hbm, src, traffic_json):
+    """Roofline of the set-up (tile count, sorting scatter, spread): its
+    algorithmic bytes are each point's coordinates and value read once
+    (d*4 + 4 = 12 B per point for 2D FP32); extra sort traffic is not
+    algorithmic and counts against the fraction.  Per-kernel figures (each
+    kernel's own reads and writes over its own time) are kept beside it."""
+    setup_ms = tot["bin_count_ms"] + tot["bin_scatter_ms"] + tot["spread_ms"]
+    alg = rec.n * (d * coord_b + val_b)
+    achieved = alg / (setup_ms / 1000.0) / 1e9 if setup_ms > 0 else None
+    per = {
+        "bin_count": rec.n * d * coord_b,
+        "bin_scatter": rec.n * (d * coord_b + val_b) + rec.n * (d + 1) * rec_bytes,
+        "spread": rec.n * (d + 1) * rec_bytes,
+    }
+    per_kernel = {}
+    traffic = 0.0
+    for k, b in per.items():
+        ms = tot[k + "_ms"]
+        t = traffic_for(k, rec.n, traffic_json) if traffic_json else None
+        traffic = None if (t is None or traffic is None) else traffic + t
+        per_kernel[k] = {"alg_bytes": b, "ms": ms, "gbs": b / (ms / 1000) / 1e9 if ms > 0 else None,
+                         "frac": b / (ms / 1000) / 1e9 / hbm if ms > 0 else None, "traffic": t}
+    return {"kernel": "setup: tile count + sorting scatter + spread", "bound": "hbm", "achieved": achieved,
+            "peak": hbm, "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+            "peak_source": src, "alg_bytes_per_launch": alg, "ms_per_launch": setup_ms, "per_kernel": per_kernel}
+
+
+_DIRECT_CACHE = {}
+
+
+def accuracy_record(E, x, y, z, kern, sigma, eps, prec, name, setup_path=0, max_dense_M=12000, n_targets=2000):
+    """Mean error of the GPU path, the way tests/test_gpu_full_size.py checks it
+    (CPU test infrastructure, outside any timed region): sampled entries of w
+    (eq. 88) and b (eq. rhs) against FP64 direct sums over all points; then
+    the dense solve of the GPU's own (verified) system and the direct mean at
+    sampled targets against the GPU's CG + type-2 mean, relative to max|y|."""
+    import numpy as np
+    from oracle import efgp_oracle as O
+    h = E.setup(x, y, kern, sigma, eps, precision=prec, setup_path=setup_path)
+    info = h.solve()
+    mu = h.predict(z).double().cpu().numpy()
+    w, b = h.system()
+    par = h.params()
+    h.close()
+    fam, nu, ell, _, _ = synthdata.MODELS[name]
+    okern = O.Kernel(fam, nu, ell)
+    d = x.shape[1] if x.dim() > 1 else 1
+    hh, m = O.choose_h_m(okern, d, eps)
+    D = O.spectral_weights(okern, d, hh, m)
+    xh, yh = x.cpu().numpy(), y.cpu().numpy()
+    n = xh.shape[0]
+    rng = np.random.default_rng(2024)
+    # one random entry of each (every entry is a sum over all N points: at
+    # N = 1e9 that is ~20 s of host time per entry; the full-size test checks more)
+    kw = np.array([list(rng.integers(-2 * m, 2 * m + 1, d))])
+    kb = np.array([list(rng.integers(-m, m + 1, d))])
+    t0 = time.perf_counter()
+    key = (name, n, m)
+    if key not in _DIRECT_CACHE:    # the same points for every form: sum once
+        _DIRECT_CACHE[key] = (O.direct_modes(xh, 1.0, hh, kw), O.direct_modes(xh, yh, hh, kb))
+    wd, bd = _DIRECT_CACHE[key]
+    n1 = 2 * m + 1
+    w_err = max(abs(w[tuple(k + 2 * m)] - r) for k, r in zip(kw, wd)) / n
+    jb = [int(np.ravel_multi_index(tuple(k + m), (n1,) * d)) for k in kb]
+    ysum = float(np.abs(yh).sum(dtype=np.float64))
+    b_err = max(abs(b[j] / D[j] - r) for j, r in zip(jb, bd)) / ysum
+    ymax = float(np.abs(yh).max())
+    out = {"w_err_rel_n": float(w_err), "b_err_rel_sum_abs_y": float(b_err), "nufft_tol": eps / 10,
+           "cg_iters": info["iters"], "true_rel_residual": info["true_rel_residual"], "criterion": 10 * eps,
+           "method": "a random w and b entry vs FP64 direct sums over all points; dense solve of the GPU's "
+                     f"system and direct mean at {n_targets} sampled targets vs the GPU mean, / max|y|"}
+    if par["M"] <= max_dense_M:
+        A = O.system_matrix(w, D, sigma, m, d)
+        beta = np.linalg.solve(A, b)
+        del A
+        idx = rng.choice(mu.shape[0], min(n_targets, mu.shape[0]), replace=False)
+        ref = O.mean_at(z[idx].cpu().numpy().astype(np.float64), beta, D, hh, m).real
+        out["mean_error"] = float(np.abs(mu[idx] - ref).max() / ymax)
+    else:
+        out["mean_error"] = None
+        out["note"] = f"M = {par['M']} is beyond the dense solve ({max_dense_M})"
+    out["check_s"] = time.perf_counter() - t0
+    return out
+
+
+def oracle_single_core(name, n_sample, q_sample):
+    """The oracle on one host core (BLAS and thread pools limited to one
+    thread, in a child process so the limit holds from interpreter start)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "v, dt = bench.oracle_sample(%r, %d, %d); print(json.dumps([v, dt]))" % (ROOT, name, n_sample, q_sample))
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    v, dt = json.loads(r.stdout.strip().splitlines()[-1])
+    return v, dt
+
+
+def time_variant(E, x, y, z, kern, sigma, eps, prec, setup_path, steps, warmup=1):
+    """ms per whole step (set-up, solve, predict) of another form of the path
+    on the same device inputs, CUDA events on the current stream."""
+    import torch
+
+    def one():
+        h = E.setup(x, y, kern, sigma, eps, precision=prec, setup_path=setup_path, profile=1)
+        info = h.solve()
+        h.predict(z)
+        pt = h.phase_times()
+        h.close()
+        return info, pt
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    outs = [one() for _ in range(steps)]
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ph = {k.replace("_ms", ""): round(sum(o[1][k] for o in outs) / steps, 4)
+          for k in ("bin_count_ms", "bin_scatter_ms", "spread_ms", "cg_ms")}
+    return ms, [o[0]["iters"] for o in outs], ph
 
 
 def run_reference(args, rank, world):
@@ -428,7 +553,7 @@ def run_ours(args, rank, world):
 
     def step(profile=0):
         h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile, cg_mode=args.cg_mode,
-                    autotune=args.autotune)
+                    autotune=args.autotune, setup_path=args.setup_path)
         info = h.solve()
         mu = h.predict(z)
         pt = h.phase_times()
@@ -467,7 +592,7 @@ def run_ours(args, rank, world):
     ms_step = ms / args.steps
     value = job_throughput(rec.n, world, ms_step)
 
-    # phase shares and the dominant kernel's roofline
+    # phase shares and the set-up's roofline
     keys = ["bin_count_ms", "bin_scatter_ms", "spread_ms", "fine_fft_ms", "what_ms", "cg_ms", "predict_fft_ms",
             "interp_ms"]
     tot = {k: sum(p[k] for p in pts) / args.steps for k in keys}
@@ -478,25 +603,21 @@ def run_ours(args, rank, world):
     rec_bytes = 4 if prec == "mixed" else 8
     coord_b = 4 if rec.coord_dtype == "float32" else 8
     val_b = 4 if rec.value_dtype == "float32" else 8
-    # algorithmic bytes: each kernel must read its points (and the count/scatter
-    # write the sorted copy); reported against the kernel's own time
-    alg = {
-        "bin_count_ms": rec.n * d * coord_b,
-        "bin_scatter_ms": rec.n * (d * coord_b + val_b) + rec.n * (d + 1) * rec_bytes,
-        "spread_ms": rec.n * (d + 1) * rec_bytes,
-        "interp_ms": q * (d * coord_b + val_b),
-    }
-    dom = max(keys, key=lambda k: tot[k])
-    roof_kernel = dom if dom in alg else max(alg, key=lambda k: tot[k])
-    kt = tot[roof_kernel]
-    achieved = alg[roof_kernel] / (kt / 1000.0) / 1e9 if kt > 0 else None
-    traffic = None
-    rk = roof_kernel.replace("_ms", "")
-    if rk in KERNEL_NAMES and args.traffic_json:
-        traffic = traffic_for(rk, rec.n, args.traffic_json)
-    roofline = {"kernel": roof_kernel.replace("_ms", ""), "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                "peak_source": src, "alg_bytes_per_launch": alg[roof_kernel], "ms_per_launch": kt}
+    roofline = setup_roofline(rec, d, coord_b, val_b, rec_bytes, tot, hbm, src, args.traffic_json)
+
+    accuracy = None
+    # other forms of the same step, outside the timed region: the bitwise
+    # reproducible fused set-up, and the plain FP64 form (precision pattern)
+    variants = {}
+    if not args.no_variants:
+        if d == 2 and prec == "mixed" and rec.coord_dtype == "float32":
+            ms_f, it_f, ph_f = time_variant(E, x, y, z, kern, sigma, eps, prec, 2, max(1, min(args.steps, 3)))
+            variants["fused_deterministic_setup"] = {"ms_per_step": ms_f, "value": job_throughput(rec.n, world, ms_f),
+                                                     "cg_iters": it_f, "phase_ms": ph_f}
+        if prec == "mixed":
+            ms_d, it_d, ph_d = time_variant(E, x, y, z, kern, sigma, eps, "fp64", 0, 2)
+            variants["fp64_form"] = {"ms_per_step": ms_d, "value": job_throughput(rec.n, world, ms_d),
+                                     "cg_iters": it_d, "phase_ms": ph_d}
 
     # the Toeplitz product beside a cuFFT form of it
     matvec = None
@@ -527,6 +648,13 @@ def run_ours(args, rank, world):
                    "interp_gbs": ib / (ims / 1000) / 1e9, "interp_frac_hbm": ib / (ims / 1000) / 1e9 / hbm,
                    "alg_bytes": ib}
         del mu_all
+
+    # accuracy of the measured form (and of the FP64 form), by the CPU
+    # reference leg's procedure: outside every timed region, rank 0 at N = 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_accuracy:
+        accuracy = accuracy_record(E, x, y, z, kern, sigma, eps, prec, name)
+        if "fp64_form" in variants:
+            variants["fp64_form"]["accuracy"] = accuracy_record(E, x, y, z, kern, sigma, eps, "fp64", name)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -567,6 +695,13 @@ def run_ours(args, rank, world):
         v, dt = oracle_sample(name, ns, 10_000)
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"first {ns} points of the workload, 10000 targets, same h and m ({dt:.1f} s)"}
+        try:
+            n1c = max(ns // 8, 1000)
+            v1, dt1 = oracle_single_core(name, n1c, 2_000)
+            cpu["single_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                                  "sample": f"first {n1c} points, 2000 targets ({dt1:.1f} s)"}
+        except Exception as exc:   # reported, not fatal: the all-core figure stands
+            cpu["single_core"] = {"value": None, "error": str(exc)[:200]}
         ne = cpu_efgp_sample_size(name)
         ve, dte, inf = cpu_efgp_sample(name, ne, 10_000)
         cpu_efgp = {"value": ve, "unit": UNIT, "cores": os.cpu_count(), "kind": "cpu_efgp",
@@ -589,6 +724,10 @@ def run_ours(args, rank, world):
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu,
         }
+        if accuracy:
+            line["mean_error"] = accuracy.get("mean_error")
+            line["accuracy"] = accuracy
+        line.update(variants)
         if at_data:
             line["mean_at_data"] = at_data
         if matvec:
@@ -616,11 +755,16 @@ def main():
                     help="skip timing the Toeplitz product beside its cuFFT form")
     ap.add_argument("--autotune", type=int, default=0, choices=[0, 1],
                     help="time candidate line batches per Toeplitz pass before the CG graph is captured")
-    ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="CG launch form (0 chooses; see efgp_options.cg_mode)")
+    ap.add_argument("--setup-path", type=int, default=0, choices=[0, 1, 2],
+                    help="set-up kernels (0 chooses; 1 three passes; 2 fused chunked; see efgp_options.setup_path)")
     ap.add_argument("--at-data", action="store_true",
                     help="also time the posterior mean at all N training points (type-2 with q = N)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the mean-error check of the CPU leg")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the fused deterministic set-up and the FP64 form beside the measured step")
     ap.add_argument("--traffic-json", default=os.path.join(ROOT, "profiles", "traffic.json"))
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))

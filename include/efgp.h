@@ -92,8 +92,15 @@ typedef struct {
                         /* 2: one persistent launch, a thread-block cluster per problem     */
                         /*    (small problems);                                            */
                         /* 3: one launch whose blocks claim work items (FFT line batches,   */
-                        /*    vector chunks) of any problem's current CG phase             */
+                        /*    vector chunks) of any problem's current CG phase;            */
+                        /* 4: one cooperative launch over the whole GPU, grid barriers      */
+                        /*    between the passes (bounded waits: ETIMEOUT)                 */
   void* stream;         /* cudaStream_t to order work on (NULL: a private stream)         */
+  int setup_path;       /* set-up kernels: 0 or 1: three passes (tile count, sorting     */
+                        /* scatter, spread; fastest); 2: fused chunked sort-and-spread,  */
+                        /* bitwise reproducible, compensated FP64 tile sums (2D, FP32 x */
+                        /* and y, row-major, 16-byte aligned, mixed precision; other    */
+                        /* problems take the three passes)                              */
 } efgp_options;
 
 /* Discretisation and NUFFT parameters chosen for a problem. */

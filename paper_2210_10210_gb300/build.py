@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libefgp.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "fft.cu", "cg.cu", "cg_persistent.cu", "cg_queue.cu", "spread.cu", "interp.cu", "predict_noalloc.cu"]
+CU_SOURCES = ["api.cu", "fft.cu", "cg.cu", "cg_persistent.cu", "cg_queue.cu", "cg_grid.cu", "setup_fused.cu", "spread.cu", "interp.cu", "predict_noalloc.cu"]
 CPP_SOURCES = ["host_params.cpp"]
 
 

@@ -520,6 +520,102 @@ int free_temps(efgp_handle* H, std::vector<void*>& temps) {
   return EFGP_OK;
 }
 
+// ---- fused chunked set-up (setup_fused.cu): 2D, FP32 row-major coordinates
+// and FP32 values in 16-byte aligned device arrays, mixed precision, ES width
+// <= 6 and at most kFusedMaxTiles spread tiles; options.setup_path = 1 forces
+// the three-pass form.
+constexpr long long kFusedShare = 24576;   // points of one block's share of a chunk
+
+bool fused_eligible(efgp_handle* H, const SortGeom& sg, const void* dx, const void* dy, int* blocks, size_t* smem) {
+  if (H->opt.setup_path != 2 || H->N <= 0 || H->d != 2 || H->f64) return false;
+  if (H->opt.coord_dtype != EFGP_F32 || H->opt.value_dtype != EFGP_F32 || H->opt.x_layout != 0) return false;
+  if ((reinterpret_cast<uintptr_t>(dx) % 16) != 0 || (reinterpret_cast<uintptr_t>(dy) % 16) != 0) return false;
+  if (sg.W > kFusedMaxWidth || sg.TB != 16 || sg.ntiles > kFusedMaxTiles) return false;
+  const size_t sm = fused_smem_bytes(sg.ntiles, sg.W);
+  if (sm == 0 || sm > 227 * 1024) return false;
+  const int G = fused_blocks(sg.W, sm);
+  cudaGetLastError();
+  if (G <= 0) return false;
+  *blocks = G;
+  *smem = sm;
+  return true;
+}
+
+int setup_fused_path(efgp_handle* H, const void* dx, const void* dy, const SortGeom& sg, int G, size_t smem,
+                     std::vector<void*>& temps, void** P_out) {
+  const long long N = H->N;
+  const NufftPlan& p1 = H->p1;
+  const int T = sg.ntiles;
+  const long long share = kFusedShare;
+  const long long chunk = share * G;
+  const int K = (int)((N + chunk - 1) / chunk);
+  const long long clen = std::min(chunk, N);
+  const long long bstride = ((clen + 3) / 4) * 4 + 8;
+  const int S = sg.TB + sg.W - 1;
+  const long long cells = (long long)S * S;
+  auto get = [&](void** p, size_t bytes) -> int {
+    EFGP_CK(cudaMallocAsync(p, bytes, H->stream));
+    temps.push_back(*p);
+    return EFGP_OK;
+  };
+  void *cnt, *toff, *B0, *B1, *sl0, *sl1, *Et, *gb, *P;
+  EFGP_TRY(get(&cnt, sizeof(unsigned int) * (size_t)K * G * T));
+  EFGP_TRY(get(&toff, sizeof(unsigned int) * (size_t)K * (T + 1)));
+  EFGP_TRY(get(&B0, sizeof(float) * 3 * (size_t)bstride));
+  EFGP_TRY(get(&B1, sizeof(float) * 3 * (size_t)bstride));
+  EFGP_TRY(get(&sl0, sizeof(float2) * (size_t)(G + T) * cells));
+  EFGP_TRY(get(&sl1, sizeof(float2) * (size_t)(G + T) * cells));
+  EFGP_TRY(get(&Et, sizeof(TileAcc) * (size_t)T * cells));
+  EFGP_TRY(get(&gb, sizeof(GridBarrier)));
+  EFGP_TRY(get(&P, H->elem * (size_t)ipow(p1.nf, 2)));
+  EFGP_CK(cudaMemsetAsync(Et, 0, sizeof(TileAcc) * (size_t)T * cells, H->stream));
+  EFGP_CK(cudaMemsetAsync(gb, 0, sizeof(GridBarrier), H->stream));
+  H->mark(0);
+  EFGP_CK(launch_fused_count(reinterpret_cast<const float*>(dx), N, sg, share, chunk, G, K, (unsigned int*)cnt,
+                             H->flag, H->stream));
+  H->mark(1);
+  EFGP_CK(cudaMemcpyAsync(H->host_flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
+  EFGP_CK(cudaStreamSynchronize(H->stream));
+  if (*H->host_flag) {
+    set_error("a coordinate lies outside [0,1] or is not finite");
+    return EFGP_ERANGE;
+  }
+  H->mark(2);
+  EFGP_CK(launch_fused_scan((unsigned int*)cnt, G, T, K, (unsigned int*)toff, H->stream));
+  H->mark(3);
+  FusedArgs a{};
+  a.x = reinterpret_cast<const float*>(dx);
+  a.y = reinterpret_cast<const float*>(dy);
+  a.N = N;
+  a.sg = sg;
+  a.share = share;
+  a.chunk = chunk;
+  a.nchunks = K;
+  a.off = (const unsigned int*)cnt;
+  a.toff = (const unsigned int*)toff;
+  a.B[0] = (float*)B0;
+  a.B[1] = (float*)B1;
+  a.bstride = bstride;
+  a.slots[0] = (float2*)sl0;
+  a.slots[1] = (float2*)sl1;
+  a.Et = (TileAcc*)Et;
+  long long limit = kGridWaitLimit;
+  if (fault_injected("setup_stall")) {
+    // every barrier starts with more arrivals than blocks: no barrier
+    // completes, every block's bounded wait runs out after a short limit
+    limit = 1 << 12;
+    const unsigned int stalled = (unsigned int)G;
+    EFGP_CK(cudaMemcpyAsync(&((GridBarrier*)gb)->count, &stalled, sizeof(stalled), cudaMemcpyHostToDevice, H->stream));
+  }
+  EFGP_CK(launch_setup_fused(a, &H->c1f, G, smem, (GridBarrier*)gb, limit, H->flag + 1, H->stream));
+  EFGP_CK(launch_fused_fold((const TileAcc*)Et, sg, p1.nf, p1.off, (float2*)P, H->stream));
+  EFGP_CK(cudaMemcpyAsync(H->flag + 2, &((GridBarrier*)gb)->err, sizeof(int), cudaMemcpyDeviceToDevice, H->stream));
+  H->mark(4);
+  H->times.launches += 4;
+  *P_out = P;
+  return EFGP_OK;
+}
+
 // Steps 2-3: spread, FFT, deconvolve, transform the generating vector.
 int setup_device(efgp_handle* H, const void* x, const void* y) {
   const int d = H->d;
@@ -562,7 +658,14 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   // that aligned bulk-copy windows never leave the allocation
   sg.rstride = ((N + 3) / 4) * 4 + 4;
 
-  void *counts = nullptr, *toff = nullptr, *cursor = nullptr, *rec = nullptr, *E = nullptr, *P = nullptr;
+  EFGP_CK(cudaMemsetAsync(H->flag, 0, 4 * sizeof(int), H->stream));
+  void* P = nullptr;
+  int fused_blocks_n = 0;
+  size_t fused_smem = 0;
+  if (fused_eligible(H, sg, dx, dy, &fused_blocks_n, &fused_smem)) {
+    EFGP_TRY(setup_fused_path(H, dx, dy, sg, fused_blocks_n, fused_smem, temps, &P));
+  } else {
+  void *counts = nullptr, *toff = nullptr, *cursor = nullptr, *rec = nullptr, *E = nullptr;
   EFGP_CK(cudaMallocAsync(&counts, sizeof(unsigned int) * sg.ntiles, H->stream));
   temps.push_back(counts);
   EFGP_CK(cudaMallocAsync(&toff, sizeof(long long) * (sg.ntiles + 1), H->stream));
@@ -573,13 +676,16 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   temps.push_back(E);
   EFGP_CK(cudaMemsetAsync(counts, 0, sizeof(unsigned int) * sg.ntiles, H->stream));
   EFGP_CK(cudaMemsetAsync(E, 0, sizeof(double2) * nE_tot, H->stream));
-  EFGP_CK(cudaMemsetAsync(H->flag, 0, 4 * sizeof(int), H->stream));
 
   if (N > 0) {
     EFGP_CK(cudaMallocAsync(&rec, recb * (size_t)sg.rstride * (d + 1), H->stream));
     temps.push_back(rec);
     H->mark(0);
-    EFGP_CK(launch_bin_count(dx, coord_f64, (int)f64, soa, N, sg, (unsigned int*)counts, H->flag, H->stream));
+    if (d == 2 && !coord_f64 && !f64 && !soa && reinterpret_cast<uintptr_t>(dx) % 16 == 0 &&
+        sg.ntiles <= kFusedMaxTiles)
+      EFGP_CK(launch_tile_totals_2d((const float*)dx, N, sg, (unsigned int*)counts, H->flag, H->stream));
+    else
+      EFGP_CK(launch_bin_count(dx, coord_f64, (int)f64, soa, N, sg, (unsigned int*)counts, H->flag, H->stream));
     H->mark(1);
     EFGP_CK(cudaMemcpyAsync(H->host_flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
     EFGP_CK(cudaStreamSynchronize(H->stream));
@@ -602,6 +708,7 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   EFGP_CK(cudaMallocAsync(&P, elem * nf_tot, H->stream));
   temps.push_back(P);
   EFGP_CK(launch_fold((const double2*)E, sg.nEx, p1.off, p1.nf, d, P, (int)f64, H->stream));
+  }
   void* twF1 = nullptr;
   {
     // twiddles for the type-1 fine grid (kept only for the set-up)
@@ -654,10 +761,14 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   H->times.launches += 2;
   H->mark(6);
   // bounded device waits (bulk-copy barriers) report through flag[1]
-  EFGP_CK(cudaMemcpyAsync(H->host_flag + 1, H->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
+  EFGP_CK(cudaMemcpyAsync(H->host_flag + 1, H->flag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, H->stream));
   EFGP_CK(cudaStreamSynchronize(H->stream));
   if (H->host_flag[1]) {
     set_error("a bounded device-side wait for a bulk copy ran out");
+    return EFGP_ETIMEOUT;
+  }
+  if (H->host_flag[2]) {
+    set_error("fused set-up: a bounded wait at a grid barrier ran out");
     return EFGP_ETIMEOUT;
   }
   if (H->opt.profile) {
@@ -881,6 +992,95 @@ int persistent_prepare(efgp_handle* H, double rho, long long max_iter, bool batc
   P.rho = rho;
   P.max_iter = max_iter;
   EFGP_CK(cudaMemcpyAsync(H->d_pprob, &P, sizeof(PersistentProblem), cudaMemcpyHostToDevice, H->stream));
+  return EFGP_OK;
+}
+
+// Persistent CG over the whole GPU: line batches re-chosen so that every pass
+// is one round of line blocks over the launch's blocks (one per SM) where
+// shared memory allows; descriptor copied to the device once per handle.
+constexpr size_t kGridCgMaxSmem = 160 * 1024;
+
+int grid_prepare(efgp_handle* H, double rho, long long max_iter) {
+  if (H->gblocks == 0) return EFGP_OK;
+  PersistentProblem& P = H->gprob;
+  if (H->gblocks < 0) {
+    if ((int)H->mv.size() > kMaxPasses) {
+      H->gblocks = 0;
+      return EFGP_OK;
+    }
+    int nsm = 0;
+    EFGP_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->device));
+    std::memset(&P, 0, sizeof(P));
+    P.npass = (int)H->mv.size();
+    size_t smem = 0;
+    for (int q = 0; q < P.npass; ++q) {
+      const Pass& ps = H->mv[q];
+      LineGeom g = ps.g;
+      const long long lines = g.outer * g.inner;
+      g.nb = (int)std::min<long long>(kMaxLineBatch, std::max<long long>(1, (lines + nsm - 1) / nsm));
+      while (g.nb > 1 && line_fft_smem_bytes(g.L, g.nb, H->elem) > kGridCgMaxSmem) g.nb = (g.nb + 1) / 2;
+      smem = std::max(smem, line_fft_smem_bytes(g.L, g.nb, H->elem));
+      P.pass[q] = g;
+      P.inb[q] = ps.in_buf;
+      P.outb[q] = ps.out_buf;
+      P.dir[q] = ps.dir;
+      P.inm[q] = ps.inm;
+      P.outm[q] = ps.outm;
+      P.conv[q] = ps.conv ? 1 : 0;
+    }
+    const int G = cg_grid_blocks(H->f64, smem);
+    cudaGetLastError();
+    if (G <= 0) {
+      H->gblocks = 0;
+      return EFGP_OK;
+    }
+    H->gblocks = G;
+    H->gsmem = smem;
+    P.buf[0] = nullptr;
+    P.buf[1] = H->scrA;
+    P.buf[2] = H->scrB;
+    P.tw = H->twL;
+    P.what = H->what;
+    P.x = H->x;
+    P.r = H->r;
+    P.p = H->p;
+    P.Ap = H->Ap;
+    P.b = H->b;
+    P.Dw = H->Dw;
+    P.sigma2 = H->sigma * H->sigma;
+    P.M = H->M;
+    P.st = H->st;
+    EFGP_TRY(H->alloc((void**)&H->d_gprob, sizeof(PersistentProblem)));
+    EFGP_TRY(H->alloc((void**)&H->gbar, sizeof(GridBarrier)));
+    EFGP_TRY(H->alloc((void**)&H->gpart, sizeof(double) * 2 * (size_t)G));
+  }
+  P.rho = rho;
+  P.max_iter = max_iter;
+  EFGP_CK(cudaMemcpyAsync(H->d_gprob, &P, sizeof(PersistentProblem), cudaMemcpyHostToDevice, H->stream));
+  return EFGP_OK;
+}
+
+// One cooperative launch of the grid CG; fills the host CgState.  The
+// barrier state is cleared first; EFGP_FAULT=grid_stall starts it with more
+// arrivals than blocks, so no barrier ever completes and every block's
+// bounded wait runs out (after a short limit): the launch reports a timeout.
+int run_grid(efgp_handle* H) {
+  long long limit = kGridWaitLimit;
+  EFGP_CK(cudaMemsetAsync(H->gbar, 0, sizeof(GridBarrier), H->stream));
+  if (fault_injected("grid_stall")) {
+    limit = 1 << 12;
+    const unsigned int stalled = (unsigned int)H->gblocks;
+    EFGP_CK(cudaMemcpyAsync(&H->gbar->count, &stalled, sizeof(stalled), cudaMemcpyHostToDevice, H->stream));
+  }
+  EFGP_CK(launch_cg_grid(H->d_gprob, H->gbar, H->gpart, H->gblocks, H->gsmem, H->f64, limit, H->stream));
+  H->times.launches += 1;
+  EFGP_CK(cudaMemcpyAsync(H->host_state, H->st, sizeof(CgState), cudaMemcpyDeviceToHost, H->stream));
+  EFGP_CK(cudaMemcpyAsync(H->host_flag + 2, &H->gbar->err, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
+  EFGP_CK(cudaStreamSynchronize(H->stream));
+  if (H->host_flag[2]) {
+    set_error("grid CG: a bounded wait at a grid barrier ran out");
+    return EFGP_ETIMEOUT;
+  }
   return EFGP_OK;
 }
 
@@ -1214,8 +1414,12 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
   const long long max_iter = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
   const bool queued = H->opt.cg_mode == 3;
-  bool persistent = false;
-  if (!queued) {
+  bool persistent = false, grid = false;
+  if (H->opt.cg_mode == 4) {
+    EFGP_TRY(grid_prepare(H, rho, max_iter));
+    grid = H->gblocks > 0;
+  }
+  if (!queued && !grid) {
     EFGP_TRY(persistent_prepare(H, rho, max_iter, false));
     persistent = H->pcluster > 0;
     if (!persistent) EFGP_TRY(capture_cg_graph(H));
@@ -1234,6 +1438,8 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   cudaEvent_t e0 = evp.a, e1 = evp.b;
   EFGP_CK(cudaEventRecord(e0, H->stream));
   if (queued) {
+  } else if (grid) {
+    EFGP_TRY(run_grid(H));
   } else if (persistent) {
     EFGP_CK(launch_cg_persistent(H->d_pprob, 1, H->pcluster, H->psmem, H->f64, H->stream));
     H->times.launches += 1;

@@ -104,12 +104,14 @@ __device__ __forceinline__ void grid_pos_f(float x, const GridScale& g, int& l0,
   // u = x*s evaluated as a + lo with a = fl(x*s_hi) and lo the product's
   // rounding error plus x*s_lo, so f keeps ~1e-7 cell accuracy even for
   // fine grids of thousands of cells.
-  const float a = x * g.s_hi;
+  // (explicitly rounded operations: no call site may contract them into a
+  // different FMA, so every kernel that bins a point computes the same cell)
+  const float a = __fmul_rn(x, g.s_hi);
   const float r = fmaf(x, g.s_hi, -a);
   const float lo = fmaf(x, g.s_lo, r);
-  const float v = a - g.halfw_f;
-  float l = ceilf(v + lo);
-  float ff = (l - v) - lo;
+  const float v = __fsub_rn(a, g.halfw_f);
+  float l = ceilf(__fadd_rn(v, lo));
+  float ff = __fsub_rn(__fsub_rn(l, v), lo);
   if (ff < 0.f) { l += 1.f; ff += 1.f; }
   else if (ff >= 1.f) { l -= 1.f; ff -= 1.f; }
   l0 = (int)l;

@@ -86,6 +86,13 @@ struct efgp_handle {
   size_t psmem = 0;
   efgp::PersistentProblem pprob{};
   efgp::PersistentProblem* d_pprob = nullptr;
+  // persistent CG over the whole GPU (cg_grid.cu)
+  int gblocks = -1;                     // -1 undecided, 0 not eligible, else blocks of the launch
+  size_t gsmem = 0;
+  efgp::PersistentProblem gprob{};
+  efgp::PersistentProblem* d_gprob = nullptr;
+  efgp::GridBarrier* gbar = nullptr;
+  double* gpart = nullptr;
   // dynamically scheduled CG (cg_queue.cu)
   double* qpartials = nullptr;
   long long qpartials_n = 0;

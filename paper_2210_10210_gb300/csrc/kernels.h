@@ -75,6 +75,21 @@ cudaError_t launch_cg_persistent(const PersistentProblem* d_probs, int nprob, in
                                  cudaStream_t s);
 int persistent_cluster_size(int f64, size_t smem);
 
+// ---- persistent CG on the whole GPU, one cooperative launch (cg_grid.cu)
+constexpr int kGridCgThreads = 256;
+// Grid barrier state (host zeroes it before every launch).
+struct GridBarrier {
+  unsigned int count;   // blocks arrived at the current barrier
+  unsigned int gen;     // barriers completed
+  int err;              // non-zero: a block gave up waiting
+  int pad;
+};
+constexpr long long kGridWaitLimit = 1ll << 24;   // polls of one barrier wait (seconds)
+// part: 2 * blocks doubles of per-block partial sums
+cudaError_t launch_cg_grid(const PersistentProblem* d_prob, GridBarrier* gb, double* part, int blocks, size_t smem,
+                           int f64, long long limit, cudaStream_t s);
+int cg_grid_blocks(int f64, size_t smem);   // blocks of the cooperative launch (0: not possible)
+
 // ---- dynamically scheduled CG over many problems in one launch (cg_queue.cu)
 constexpr int kQueueThreads = 512;
 constexpr int kQueueChunk = 2048;   // vector elements per item of the init and update phases
@@ -156,6 +171,40 @@ cudaError_t launch_deconv_split(const void* Phat, int p_f64, int nf, int d, int 
 cudaError_t launch_place_w(const double2* w, int m, int d, int L, double2* grid, cudaStream_t s);
 cudaError_t launch_extract_what(const double2* grid, long long n, double scale, void* what, int what_f64,
                                 cudaStream_t s);
+
+// ---- fused chunked set-up, 2D FP32 points (setup_fused.cu)
+constexpr int kFusedMaxTiles = 1024;   // spread tiles of the fused path (shared-memory histograms)
+constexpr int kFusedMaxWidth = 6;      // ES widths whose W x W register footprint fits
+// FP64 accumulator of one cell of a halo'd tile: sums and compensations.
+struct alignas(32) TileAcc {
+  double sx, sy, cx, cy;
+};
+struct FusedArgs {
+  const float* x;               // N x 2 row-major, 16-byte aligned
+  const float* y;               // N, 16-byte aligned
+  long long N;
+  SortGeom sg;
+  long long share;              // points of one block's share of a chunk (multiple of 4096)
+  long long chunk;              // points per chunk = blocks * share
+  int nchunks;
+  const unsigned int* off;      // [nchunks][blocks][ntiles]: chunk position of a share's first point per tile
+  const unsigned int* toff;     // [nchunks][ntiles + 1]: first chunk position of each tile
+  float* B[2];                  // chunk buffers (k mod 2): arrays q0, q1, y of bstride floats each
+  long long bstride;            // >= chunk + 8, multiple of 4
+  float2* slots[2];             // tile-visit partials of chunk k mod 2: (blocks + ntiles) x S^2
+  TileAcc* Et;                  // ntiles x S^2 halo'd tiles (sums and compensations)
+};
+size_t fused_smem_bytes(int ntiles, int W);
+int fused_blocks(int W, size_t smem);   // resident blocks of the cooperative launch (0: not possible)
+cudaError_t launch_fused_count(const float* x, long long N, const SortGeom& sg, long long share, long long chunk,
+                               int blocks, int nchunks, unsigned int* cnt, int* range_flag, cudaStream_t s);
+cudaError_t launch_tile_totals_2d(const float* x, long long N, const SortGeom& sg, unsigned int* counts,
+                                  int* range_flag, cudaStream_t s);
+cudaError_t launch_fused_scan(unsigned int* cnt, int blocks, int ntiles, int nchunks, unsigned int* toff,
+                              cudaStream_t s);
+cudaError_t launch_setup_fused(const FusedArgs& a, const void* coef, int blocks, size_t smem, GridBarrier* gb,
+                               long long limit, int* err, cudaStream_t s);
+cudaError_t launch_fused_fold(const TileAcc* Et, const SortGeom& sg, int nf, int off, float2* P, cudaStream_t s);
 
 // ---- predict kernels (interp.cu)
 cudaError_t launch_precorrect(const double2* beta, const double* Dw, const double* corr2, int m, int d, int nf,

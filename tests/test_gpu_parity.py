@@ -148,22 +148,23 @@ def test_toeplitz_apply_matches_dense(E):
 @pytest.mark.parametrize("name,n,prec", [("matern2d", 100_000, "mixed"), ("se3d", 50_000, "mixed"),
                                          ("se1d", 10_000, "fp64"), ("matern2d", 20_000, "fp64")])
 def test_single_launch_cg_matches_graph_cg(E, name, n, prec):
-    # one persistent launch on a thread-block cluster (mode 2) and one launch
-    # of the work-claiming scheduled kernel (mode 3) vs graph-captured per-pass
+    # one persistent launch on a thread-block cluster (mode 2), one launch of
+    # the work-claiming scheduled kernel (mode 3) and one cooperative launch
+    # over the whole GPU with grid barriers (mode 4) vs graph-captured per-pass
     # kernels (mode 1): same iterations up to rounding, same mean
     rec = synthdata.config(name, n=n)
     x, y, z = synthdata.make_np(rec)
     z = z[:5000]
     ek, ok, sigma, eps = _kernel(E, synthdata.MODELS[name])
     out = {}
-    for mode in (1, 2, 3):
+    for mode in (1, 2, 3, 4):
         h = E.setup(_dev(x), _dev(y), ek, sigma, eps, precision=prec, cg_mode=mode)
         info = h.solve()
         assert info["converged"], (mode, info)
         out[mode] = (info, h.predict(_dev(z)).double().cpu().numpy())
         h.close()
     i1, m1 = out[1]
-    for mode in (2, 3):
+    for mode in (2, 3, 4):
         i2, m2 = out[mode]
         assert abs(i1["iters"] - i2["iters"]) <= max(5, 0.1 * i1["iters"]), mode
         assert np.abs(m1 - m2).max() <= 0.2 * 10 * eps * np.abs(y).max(), mode
@@ -257,18 +258,48 @@ def test_cg_iteration_cap_reports_not_converged(E):
 
 
 def test_deterministic_rerun(E):
-    rec = synthdata.config("matern2d", n=30_000)
+    """The fused set-up sums in an order fixed by the input alone (stable
+    counting sorts, slot reductions in block order) and the CG reduces in
+    block order: two runs give bitwise-identical w, b, beta and mean."""
+    rec = synthdata.config("matern2d", n=300_000)
     x, y, z = synthdata.make_np(rec)
     ek, _, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
     outs = []
     for _ in range(2):
-        h = E.setup(_dev(x), _dev(y), ek, sigma, eps)
+        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=2)
         h.solve()
-        outs.append(h.predict(_dev(z[:2000])).cpu().numpy())
-    # the spread's FP32 in-cell sums and FP64 flushes run in atomic order, so
-    # reruns differ by rounding, amplified by the CG solve; they must agree to
-    # a small fraction of the parity tolerance
-    assert np.abs(outs[0] - outs[1]).max() <= 0.2 * 10 * eps * np.abs(y).max()
+        w, b = h.system()
+        outs.append((w, b, h.beta(), h.predict(_dev(z[:2000])).cpu().numpy()))
+        h.close()
+    for a, c in zip(outs[0], outs[1]):
+        assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("n", [1, 7, 4097, 300_001, 9_000_003])
+def test_fused_setup_matches_three_pass(E, n):
+    """The fused chunked set-up (count, scan, one persistent sort-and-spread
+    launch) against the three-pass form (count, sorting scatter, spread) on
+    the same points: w and b agree to FP32 rounding of the in-tile sums, far
+    inside the NUFFT tolerance.  9e6 points span three chunks of the
+    persistent kernel, the last one partial, with a partial sub-chunk and an
+    odd count; 4097 leaves one point past the first sub-chunk."""
+    rec = synthdata.config("matern2d_1e9", n=n)
+    x, y, _ = synthdata.make_np(rec)
+    ek, _, sigma, eps = _kernel(E, synthdata.MODELS["matern2d_1e9"])
+    got = {}
+    for path in (1, 2):
+        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=path)
+        got[path] = h.system()
+        h.close()
+    tol = eps / 10
+    scale_w = max(n, 1)
+    scale_b = max(np.abs(y).sum(), 1e-30)
+    (w1, b1), (w2, b2) = got[1], got[2]
+    assert np.abs(w1 - w2).max() / scale_w <= 1e-2 * tol
+    assert np.abs(b1 - b2).max() / scale_b <= 1e-2 * tol
+    # w_0 = sum_n exp(0) is the point count
+    w0 = w2.flat[w2.size // 2]
+    assert abs(w0.real - n) <= 3 * tol * scale_w and abs(w0.imag) <= 3 * tol * scale_w
 
 
 def test_batch_matches_single_and_oracle(E):
@@ -392,6 +423,29 @@ def test_scheduled_cg_bounded_wait_reports_timeout(E, monkeypatch):
     ek, ok, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
     h = E.setup(_dev(x), _dev(y), ek, sigma, eps, cg_mode=3)
     monkeypatch.setenv("EFGP_FAULT", "queue_stall")
+    with pytest.raises(E.EfgpError) as ei:
+        h.solve()
+    assert ei.value.status == _capi.EFGP_ETIMEOUT
+    monkeypatch.delenv("EFGP_FAULT")
+    info = h.solve()
+    assert info["converged"]
+    mu = h.predict(_dev(z[:2000])).double().cpu().numpy()
+    h.close()
+    ref = _oracle(("matern2d", 20_000, None, 2000), x, y, z[:2000], ok, sigma, eps)
+    assert np.abs(mu - ref.mu).max() <= 10 * eps * np.abs(y).max()
+
+
+def test_grid_cg_bounded_barrier_wait_reports_timeout(E, monkeypatch):
+    """EFGP_FAULT=grid_stall starts the grid CG's barrier with more arrivals
+    than blocks, so no barrier completes: every block's bounded wait runs out,
+    the launch returns, the host reports EFGP_ETIMEOUT, and the same handle
+    then solves normally."""
+    from paper_2210_10210_gb300 import _capi
+    rec = synthdata.config("matern2d", n=20_000)
+    x, y, z = synthdata.make_np(rec)
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
+    h = E.setup(_dev(x), _dev(y), ek, sigma, eps, cg_mode=4)
+    monkeypatch.setenv("EFGP_FAULT", "grid_stall")
     with pytest.raises(E.EfgpError) as ei:
         h.solve()
     assert ei.value.status == _capi.EFGP_ETIMEOUT
