@@ -214,11 +214,12 @@ def cpu_sample_size(name):
             "matern2d_table4": 50_000, "matern2d_table5": 50_000}.get(name, 100_000)
 
 
-# Plain FP64 where FP32 grids cannot represent the system: se1d asks for
-# eps = 1e-6, and at N = 1e9 with sigma = 0.1 (N / sigma^2 = 1e11) the FP32
-# error of the Toeplitz product (~1e-7 N max D^2) exceeds sigma^2, so the
-# mixed-precision operator is not positive definite and CG breaks down.
-DEFAULT_PRECISION = {"se1d": "fp64", "matern2d_table4": "fp64"}
+# se1d asks for eps = 1e-6, beyond the FP32 path: plain FP64.  At N = 1e9
+# with sigma = 0.1 (N / sigma^2 = 1e11) the FP32 error of the Toeplitz product
+# (~1e-7 N max D^2) exceeds sigma^2, so the all-FP32-FFT operator is not
+# positive definite and CG breaks down: the set-up stays FP32, the Toeplitz
+# products and CG run in FP64 (mixed_cg64).
+DEFAULT_PRECISION = {"se1d": "fp64", "matern2d_table4": "mixed_cg64"}
 
 # The paper's total run times (set-up, solve and the mean on the 1000^2 target
 # grid) for the exact N = 1e9 workloads of Sec. 5.4, on its 12-core desktop:
@@ -600,7 +601,7 @@ def run_ours(args, rank, world):
     iters = [i["iters"] for i in infos]
     hbm, src = _peaks()
     d = rec.d
-    rec_bytes = 4 if prec == "mixed" else 8
+    rec_bytes = 8 if prec == "fp64" else 4
     coord_b = 4 if rec.coord_dtype == "float32" else 8
     val_b = 4 if rec.value_dtype == "float32" else 8
     roofline = setup_roofline(rec, d, coord_b, val_b, rec_bytes, tot, hbm, src, args.traffic_json)
@@ -610,11 +611,11 @@ def run_ours(args, rank, world):
     # reproducible fused set-up, and the plain FP64 form (precision pattern)
     variants = {}
     if not args.no_variants:
-        if d == 2 and prec == "mixed" and rec.coord_dtype == "float32":
+        if d == 2 and prec != "fp64" and rec.coord_dtype == "float32":
             ms_f, it_f, ph_f = time_variant(E, x, y, z, kern, sigma, eps, prec, 2, max(1, min(args.steps, 3)))
             variants["fused_deterministic_setup"] = {"ms_per_step": ms_f, "value": job_throughput(rec.n, world, ms_f),
                                                      "cg_iters": it_f, "phase_ms": ph_f}
-        if prec == "mixed":
+        if prec != "fp64":
             ms_d, it_d, ph_d = time_variant(E, x, y, z, kern, sigma, eps, "fp64", 0, 2)
             variants["fp64_form"] = {"ms_per_step": ms_d, "value": job_throughput(rec.n, world, ms_d),
                                      "cg_iters": it_d, "phase_ms": ph_d}
@@ -712,7 +713,7 @@ def run_ours(args, rank, world):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": paper_ratio(name, rec.n, value), "dtype": "f32+f64" if prec == "mixed" else "f64",
+            "vs_baseline": paper_ratio(name, rec.n, value), "dtype": "f64" if prec == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(name, rec, model), "precision": prec, "m": par["m"],
                        "M": par["M"], "L": par["L"], "nf1": par["nf1"], "w1": par["w1"], "nf2": par["nf2"],
@@ -747,7 +748,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="matern2d_1e9")
     ap.add_argument("--n", type=int, default=None, help="override the point count")
-    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64"])
+    ap.add_argument("--precision", default=None, choices=[None, "mixed", "fp64", "mixed_cg64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--once", action="store_true", help="run one untimed step and exit (profiling target)")
     ap.add_argument("--batch-count", type=int, default=64)

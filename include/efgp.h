@@ -55,7 +55,13 @@ typedef enum {
 } efgp_status;
 
 typedef enum { EFGP_KERNEL_SE = 0, EFGP_KERNEL_MATERN = 1 } efgp_kernel_family;
-typedef enum { EFGP_MIXED = 0, EFGP_FP64 = 1 } efgp_precision;
+/* EFGP_MIXED: FP32 spreading, fine-grid and Toeplitz FFTs, FP64 CG vectors and
+ * scalars; EFGP_FP64: everything FP64; EFGP_MIXED_CG64: FP32 spreading (FP32
+ * records and tiles, FP64 flush), FP64 fine grid, Toeplitz FFTs, CG and type-2
+ * (for systems whose FP32
+ * Toeplitz product error, ~1e-7 N max D^2, would exceed sigma^2); the type-1
+ * fine grid and its FFT are FP64 there too, for the same reason. */
+typedef enum { EFGP_MIXED = 0, EFGP_FP64 = 1, EFGP_MIXED_CG64 = 2 } efgp_precision;
 typedef enum { EFGP_F32 = 0, EFGP_F64 = 1 } efgp_dtype;
 
 /* Covariance kernel (eqs. Gker and Cker), scaled by `variance` (k(0)). */
@@ -68,7 +74,7 @@ typedef struct {
 
 /* Options.  Zero-initialise (or call efgp_default_options) and set fields. */
 typedef struct {
-  int precision;        /* EFGP_MIXED: FP32 spreading/FFTs, FP64 CG; EFGP_FP64: all FP64 */
+  int precision;        /* efgp_precision                                                   */
   int coord_dtype;      /* dtype of x and targets (efgp_dtype)                            */
   int value_dtype;      /* dtype of y and mu_out (efgp_dtype)                              */
   int x_layout;         /* 0: row-major N x d; 1: structure of arrays d x N               */

@@ -79,7 +79,7 @@ def _host_array(a):
 def _options(precision="mixed", coord=_capi.F32, value=_capi.F32, host_io=0, stream=None, **kw) -> efgp_options:
     o = efgp_options()
     _capi.lib().efgp_default_options(C.byref(o))
-    o.precision = {"mixed": _capi.MIXED, "fp64": _capi.FP64}[precision]
+    o.precision = {"mixed": _capi.MIXED, "fp64": _capi.FP64, "mixed_cg64": _capi.MIXED_CG64}[precision]
     o.coord_dtype = coord
     o.value_dtype = value
     o.host_io = host_io

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libefgp.so")
 EFGP_OK, EFGP_EINVAL, EFGP_ERANGE, EFGP_ENOMEM, EFGP_ENOTCONV, EFGP_ETIMEOUT, EFGP_ECUDA, EFGP_ESTATE, \
     EFGP_EUNSUPPORTED = range(9)
 KERNEL_SE, KERNEL_MATERN = 0, 1
-MIXED, FP64 = 0, 1
+MIXED, FP64, MIXED_CG64 = 0, 1, 2
 F32, F64 = 0, 1
 
 

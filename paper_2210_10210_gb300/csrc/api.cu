@@ -427,7 +427,11 @@ int plan_all_uncached(int d, long long N, const efgp_kernel* kern, double sigma,
     L = o.fft_len_override;
   }
   par->L = L;
-  const size_t elem = o.precision == EFGP_FP64 ? 16 : 8;
+  if (o.precision != EFGP_MIXED && o.precision != EFGP_FP64 && o.precision != EFGP_MIXED_CG64) {
+    set_error("unknown precision");
+    return EFGP_EINVAL;
+  }
+  const size_t elem = o.precision == EFGP_MIXED ? 8 : 16;
   const double tol = o.nufft_tol > 0 ? o.nufft_tol : eps / 10.0;
   const int maxlen = (int)(kLineFftMaxSmem / (2 * elem)) - 1;
   if (L > maxlen) {
@@ -567,7 +571,7 @@ int setup_fused_path(efgp_handle* H, const void* dx, const void* dy, const SortG
   EFGP_TRY(get(&sl1, sizeof(float2) * (size_t)(G + T) * cells));
   EFGP_TRY(get(&Et, sizeof(TileAcc) * (size_t)T * cells));
   EFGP_TRY(get(&gb, sizeof(GridBarrier)));
-  EFGP_TRY(get(&P, H->elem * (size_t)ipow(p1.nf, 2)));
+  EFGP_TRY(get(&P, sizeof(float2) * (size_t)ipow(p1.nf, 2)));
   EFGP_CK(cudaMemsetAsync(Et, 0, sizeof(TileAcc) * (size_t)T * cells, H->stream));
   EFGP_CK(cudaMemsetAsync(gb, 0, sizeof(GridBarrier), H->stream));
   H->mark(0);
@@ -621,8 +625,9 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   const int d = H->d;
   const long long N = H->N;
   const NufftPlan& p1 = H->p1;
-  const bool f64 = H->f64;
-  const size_t elem = H->elem;
+  const bool sf64 = H->sf64;             // precision of the spread records and tiles
+  const bool f64 = H->f64;               // precision of the fine grid and its FFT
+  const size_t elem = f64 ? 16 : 8;
   std::vector<void*> temps;
   struct Guard {
     efgp_handle* H;
@@ -652,7 +657,7 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   const int coord_f64 = H->opt.coord_dtype == EFGP_F64;
   const int value_f64 = H->opt.value_dtype == EFGP_F64;
   const int soa = H->opt.x_layout == 1;
-  const size_t recb = f64 ? 8 : 4;
+  const size_t recb = sf64 ? 8 : 4;
   sg.x_vec = (reinterpret_cast<uintptr_t>(dx) % 8) == 0;
   // record arrays padded to 16-byte multiples with slack after the end, so
   // that aligned bulk-copy windows never leave the allocation
@@ -681,11 +686,11 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
     EFGP_CK(cudaMallocAsync(&rec, recb * (size_t)sg.rstride * (d + 1), H->stream));
     temps.push_back(rec);
     H->mark(0);
-    if (d == 2 && !coord_f64 && !f64 && !soa && reinterpret_cast<uintptr_t>(dx) % 16 == 0 &&
+    if (d == 2 && !coord_f64 && !sf64 && !soa && reinterpret_cast<uintptr_t>(dx) % 16 == 0 &&
         sg.ntiles <= kFusedMaxTiles)
       EFGP_CK(launch_tile_totals_2d((const float*)dx, N, sg, (unsigned int*)counts, H->flag, H->stream));
     else
-      EFGP_CK(launch_bin_count(dx, coord_f64, (int)f64, soa, N, sg, (unsigned int*)counts, H->flag, H->stream));
+      EFGP_CK(launch_bin_count(dx, coord_f64, (int)sf64, soa, N, sg, (unsigned int*)counts, H->flag, H->stream));
     H->mark(1);
     EFGP_CK(cudaMemcpyAsync(H->host_flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
     EFGP_CK(cudaStreamSynchronize(H->stream));
@@ -695,11 +700,11 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
     }
     H->mark(2);
     EFGP_CK(launch_scan_tiles((unsigned int*)counts, sg.ntiles, (long long*)toff, (long long*)cursor, H->stream));
-    EFGP_CK(launch_bin_scatter(dx, coord_f64, dy, value_f64, soa, N, sg, (int)f64, (long long*)cursor, rec,
+    EFGP_CK(launch_bin_scatter(dx, coord_f64, dy, value_f64, soa, N, sg, (int)sf64, (long long*)cursor, rec,
                                H->flag + 1, H->stream));
     H->mark(3);
-    const void* coef = f64 ? (const void*)&H->c1d : (const void*)&H->c1f;
-    EFGP_CK(launch_spread(rec, (int)f64, N, sg, (const long long*)toff, coef, (double2*)E, H->flag + 1, H->stream));
+    const void* coef = sf64 ? (const void*)&H->c1d : (const void*)&H->c1f;
+    EFGP_CK(launch_spread(rec, (int)sf64, N, sg, (const long long*)toff, coef, (double2*)E, H->flag + 1, H->stream));
     H->times.launches += 4;
   }
   H->mark(4);
@@ -742,7 +747,7 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   EFGP_CK(cudaMallocAsync(&Lg, sizeof(double2) * L_tot, H->stream));
   temps.push_back(Lg);
   EFGP_CK(launch_place_w(H->w, H->n1 / 2, d, L, (double2*)Lg, H->stream));
-  if (f64) {
+  if (H->f64) {
     twLd = H->twL;
   } else {
     std::vector<double> t(2 * (size_t)L);
@@ -757,7 +762,7 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
     EFGP_CK(cudaStreamSynchronize(H->stream));
   }
   EFGP_TRY(grid_fft(H, L, -1, Lg, true, twLd));
-  EFGP_CK(launch_extract_what((const double2*)Lg, L_tot, 1.0 / (double)L_tot, H->what, (int)f64, H->stream));
+  EFGP_CK(launch_extract_what((const double2*)Lg, L_tot, 1.0 / (double)L_tot, H->what, (int)H->f64, H->stream));
   H->times.launches += 2;
   H->mark(6);
   // bounded device waits (bulk-copy barriers) report through flag[1]
@@ -1235,7 +1240,8 @@ int handle_init(efgp_handle* H, int d, long long N, const efgp_kernel* kern, dou
   H->eps = eps;
   H->opt = o;
   EFGP_TRY(plan_all(d, N, &H->kern, sigma, eps, o, &H->par, &H->p1, &H->p2));
-  H->f64 = o.precision == EFGP_FP64;
+  H->f64 = o.precision == EFGP_FP64 || o.precision == EFGP_MIXED_CG64;
+  H->sf64 = o.precision == EFGP_FP64;
   H->elem = H->f64 ? 16 : 8;
   H->M = H->par.M;
   H->n1 = 2 * H->par.m + 1;

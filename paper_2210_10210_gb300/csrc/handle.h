@@ -41,7 +41,8 @@ struct efgp_handle {
   efgp_options opt{};
   efgp_params par{};
   NufftPlan p1, p2;
-  int f64 = 0;          // FP64 grids/FFTs (plain precision)
+  int f64 = 0;          // FP64 Toeplitz products, CG grids and type-2 grids
+  int sf64 = 0;         // FP64 spread and fine grid of the set-up (plain precision)
   size_t elem = 8;      // bytes of one complex grid element
   int device = 0;
   cudaStream_t stream = nullptr;

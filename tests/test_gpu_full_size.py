@@ -82,3 +82,52 @@ def test_billion_point_workload_sampled_parity(E):
     ymax = float(np.abs(yh).max())
     err = np.abs(mu[zs_idx] - ref_mu).max()
     assert err <= 10 * eps * ymax, (err, 10 * eps * ymax)
+
+
+def test_se3d_clustered_full_size_sampled_parity(E):
+    """The 3D SE workload at its full size (N = 1e7, 30% of the points in four
+    Gaussian clusters), default options: sampled entries of w and b against
+    direct sums over all points; the dense solve (M = 23^3 = 12167) of the
+    GPU's own system and the direct mean at sampled targets against the
+    GPU's mean."""
+    name = "se3d"
+    rec = synthdata.config(name)
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    xh = synthdata.points_np(rec)
+    yh = synthdata.values_np(rec, xh)
+    zall = synthdata.targets_np(rec)
+    rng = np.random.default_rng(77)
+    zi = rng.choice(zall.shape[0], 2000, replace=False)
+    h = E.setup(torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda(), E.Kernel(fam, nu, ell), sigma, eps)
+    info = h.solve()
+    mu = h.predict(torch.from_numpy(zall[zi]).cuda()).double().cpu().numpy()
+    w, b = h.system()
+    par = h.params()
+    h.close()
+    torch.cuda.empty_cache()
+    assert info["converged"]
+    n = xh.shape[0]
+    okern = O.Kernel(fam, nu, ell)
+    hh, m = O.choose_h_m(okern, 3, eps)
+    assert m == par["m"] and abs(hh - par["h"]) < 1e-12
+    D = O.spectral_weights(okern, 3, hh, m)
+    tol = eps / 10
+    kw = np.array([[0, 0, 0], [2 * m, -2 * m, 1]] + [list(rng.integers(-2 * m, 2 * m + 1, 3)) for _ in range(3)])
+    wd = O.direct_modes(xh, 1.0, hh, kw)
+    for k, ref in zip(kw, wd):
+        got = w[k[0] + 2 * m, k[1] + 2 * m, k[2] + 2 * m]
+        assert abs(got - ref) <= 3 * tol * n, (k, got, ref)
+    n1 = 2 * m + 1
+    kb = np.array([[0, 0, 0], [m, -m, 0]] + [list(rng.integers(-m, m + 1, 3)) for _ in range(3)])
+    bd = O.direct_modes(xh, yh, hh, kb)
+    ysum = float(np.abs(yh).sum(dtype=np.float64))
+    for k, ref in zip(kb, bd):
+        j = ((k[0] + m) * n1 + (k[1] + m)) * n1 + (k[2] + m)
+        assert abs(b[j] / D[j] - ref) <= 3 * tol * ysum, (k, b[j] / D[j], ref)
+    A = O.system_matrix(w, D, sigma, m, 3)
+    beta = np.linalg.solve(A, b)
+    assert np.linalg.norm(A @ beta - b) <= 1e-6 * np.linalg.norm(b)
+    del A
+    ref_mu = O.mean_at(zall[zi], beta, D, hh, m).real
+    err = np.abs(mu - ref_mu).max()
+    assert err <= 10 * eps * np.abs(yh).max(), (err, 10 * eps * np.abs(yh).max())

@@ -1,0 +1,123 @@
+"""Parity at the paper's own problem shapes, through the C ABI.
+
+* Tables 4 and 5 (Sec. 5.4): 2D Matern-3/2, l = 0.1, eps = 1e-5, hence
+  h = 0.518 and m = 94 (M = 35721), sigma = 0.1 (Table 4) and sigma = 1.826
+  (Table 5's fixed N / sigma^2), in N-reduced twins (same kernel, noise and
+  tolerance, hence the same h and m).  M is beyond a dense solve, so the
+  reference is: exact w and b (direct sums, eqs. 88 and rhs), conjugate
+  gradients to a relative residual of 1e-13 with the CPU FFT Toeplitz product
+  (pinned against the dense assembly in tests/test_cpu_efgp.py), and the
+  direct posterior mean (eq. muws).
+* The heterogeneous 64-problem batch: every problem against its own single
+  solve, and against the oracle where the oracle is cheap (M <= 12000,
+  N <= 1e5).
+"""
+import numpy as np
+import pytest
+
+import cpu_efgp as C
+import synthdata
+from oracle import efgp_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def E():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2210_10210_gb300 as E
+    from paper_2210_10210_gb300 import build
+    build.build()
+    return E
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+_REF = {}
+
+
+def _reference(name, n, n_targets):
+    key = (name, n, n_targets)
+    if key in _REF:
+        return _REF[key]
+    rec = synthdata.config(name, n=n)
+    x, y, _ = synthdata.make_np(rec)
+    z = synthdata.targets_np(rec)
+    z = z[np.random.default_rng(11).choice(z.shape[0], n_targets, replace=False)]
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    okern = O.Kernel(fam, nu, ell)
+    h, m = O.choose_h_m(okern, 2, eps)
+    D = O.spectral_weights(okern, 2, h, m)
+    w = O.toeplitz_vector(x, h, m)
+    b = O.rhs(x, y, h, m, D)
+    A = C.ToeplitzOperator(w, D, sigma, m, 2)
+    beta, _ = C.conjugate_gradients(A, b, 1e-13)
+    mu = O.mean_at(z, beta, D, h, m).real
+    _REF[key] = (x, y, z, h, m, D, w, b, mu)
+    return _REF[key]
+
+
+@pytest.mark.parametrize("name", ["matern2d_table4", "matern2d_table5"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_cg64"])
+def test_table4_table5_shape_twins(E, name, precision):
+    x, y, z, h, m, D, w, b, mu_ref = _reference(name, 100_000, 3000)
+    assert m == 94                                    # the paper's m for l = 0.1, eps = 1e-5
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    hd = E.setup(_dev(x), _dev(y), E.Kernel(fam, nu, ell), sigma, eps, precision=precision)
+    par = hd.params()
+    assert par["m"] == m and abs(par["h"] - h) < 1e-12
+    info = hd.solve()
+    mu = hd.predict(_dev(z)).double().cpu().numpy()
+    wg, bg = hd.system()
+    hd.close()
+    tol = eps / 10
+    n = x.shape[0]
+    assert np.abs(wg - w).max() / n <= 3 * tol
+    assert (np.abs(bg - b) / D).max() / np.abs(y).sum() <= 3 * tol
+    assert info["converged"] and info["true_rel_residual"] <= 10 * eps
+    err = np.abs(mu - mu_ref).max()
+    assert err <= 10 * eps * np.abs(y).max(), (err, 10 * eps * np.abs(y).max())
+
+
+def test_sixty_four_problem_batch(E):
+    """The heterogeneous batch workload at its real size (64 problems, Matern
+    1/2 and 3/2, N log-uniform in [1e4, 1e7], m from 29 to several hundred),
+    solved by one scheduled launch: each problem against its own single
+    graph-captured solve, and the small ones against the oracle."""
+    probs = synthdata.batch_problems(seed=6, count=64)
+    items, cases = [], []
+    for rec, model in probs:
+        rec.targets, rec.n_targets = "iid", 1000
+        x, y, z = synthdata.make_np(rec)
+        fam, nu, ell, sigma, eps = model
+        items.append(dict(x=_dev(x), y=_dev(y), kernel=E.Kernel(fam, nu, ell), sigma=sigma, eps=eps))
+        cases.append((x, y, z, model))
+    B = E.batch_setup(items)
+    infos = B.solve()
+    assert all(i["converged"] for i in infos)
+    checked = 0
+    for i, (x, y, z, model) in enumerate(cases):
+        fam, nu, ell, sigma, eps = model
+        mu = B.predict(i, _dev(z)).double().cpu().numpy()
+        par = B.params(i)
+        scale = 10 * eps * np.abs(y).max()
+        h = E.setup(items[i]["x"], items[i]["y"], items[i]["kernel"], sigma, eps, cg_mode=1)
+        i1 = h.solve()
+        mu1 = h.predict(_dev(z)).double().cpu().numpy()
+        h.close()
+        # FP32 rounding in another reduction order moves the mixed CG's path
+        # (up to ~15% in iterations on the largest problems); both iterates
+        # stop at rho = eps/10 and so sit within the criterion of the exact
+        # mean: they agree to half of it
+        assert abs(i1["iters"] - infos[i]["iters"]) <= max(5, 0.2 * i1["iters"]), (i, i1, infos[i])
+        assert np.abs(mu - mu1).max() <= 0.5 * scale, i
+        if par["M"] <= 12000 and x.shape[0] <= 100_000:
+            ref = O.efgp(x, y, z, O.Kernel(fam, nu, ell), sigma, eps)
+            assert np.abs(mu - ref.mu).max() <= scale, i
+            checked += 1
+    B.close()
+    assert checked >= 5
