@@ -518,6 +518,94 @@ int stage_inputs(efgp_handle* H, const void* x, const void* y, long long N, cons
   return EFGP_OK;
 }
 
+// Host inputs copied in chunks on a second stream: the tile count of a chunk
+// of x, and later the sorting scatter of a chunk of (x, y), start as soon as
+// that chunk has arrived, so the host-to-device copy overlaps the set-up
+// (row-major x; the copies are asynchronous when the caller's memory is
+// pinned).  All x chunks are copied first, then all y chunks.
+constexpr long long kStageChunk = 1ll << 26;   // points per copy
+
+struct ChunkedStage {
+  efgp_handle* H = nullptr;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> ex, ey;
+  long long N = 0, C = kStageChunk;
+  int nch = 0;
+  size_t xpt = 0, ypt = 0;   // bytes per point
+  char* dx = nullptr;
+  char* dy = nullptr;
+  ChunkedStage() = default;
+  ChunkedStage(const ChunkedStage&) = delete;
+  ChunkedStage& operator=(const ChunkedStage&) = delete;
+  ~ChunkedStage() {
+    // nothing that frees the staging buffers may run before the copies end
+    if (H && !ey.empty() && ey.back()) cudaStreamWaitEvent(H->stream, ey.back(), 0);
+    for (cudaEvent_t e : ex) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ey) if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+  }
+  long long first(int i) const { return (long long)i * C; }
+  long long count(int i) const { return std::min(C, N - first(i)); }
+  const void* x_at(int i) const { return dx + (size_t)first(i) * xpt; }
+  const void* y_at(int i) const { return dy + (size_t)first(i) * ypt; }
+  int wait_x(int i) {
+    EFGP_CK(cudaStreamWaitEvent(H->stream, ex[i], 0));
+    return EFGP_OK;
+  }
+  int wait_y(int i) {
+    EFGP_CK(cudaStreamWaitEvent(H->stream, ey[i], 0));
+    return EFGP_OK;
+  }
+  int start(efgp_handle* h, const void* x, const void* y, long long n, std::vector<void*>& temps) {
+    H = h;
+    N = n;
+    xpt = (size_t)h->d * (h->opt.coord_dtype == EFGP_F64 ? 8 : 4);
+    ypt = h->opt.value_dtype == EFGP_F64 ? 8 : 4;
+    nch = (int)((N + C - 1) / C);
+    void *bx = nullptr, *by = nullptr;
+    EFGP_CK(cudaMallocAsync(&bx, xpt * (size_t)N, h->stream));
+    temps.push_back(bx);
+    EFGP_CK(cudaMallocAsync(&by, ypt * (size_t)N, h->stream));
+    temps.push_back(by);
+    dx = static_cast<char*>(bx);
+    dy = static_cast<char*>(by);
+    EFGP_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    // the copies start after the allocations (stream-ordered on h->stream)
+    ex.assign(nch, nullptr);
+    ey.assign(nch, nullptr);
+    {
+      cudaEvent_t ready = nullptr;
+      EFGP_CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+      const cudaError_t e1 = cudaEventRecord(ready, h->stream);
+      const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(cs, ready, 0) : e1;
+      cudaEventDestroy(ready);   // released once recorded; the wait is already queued
+      EFGP_CK(e2);
+    }
+    for (int i = 0; i < nch; ++i) {
+      EFGP_CK(cudaEventCreateWithFlags(&ex[i], cudaEventDisableTiming));
+      EFGP_CK(cudaEventCreateWithFlags(&ey[i], cudaEventDisableTiming));
+    }
+    const char* hx = static_cast<const char*>(x);
+    const char* hy = static_cast<const char*>(y);
+    for (int i = 0; i < nch; ++i) {
+      EFGP_CK(cudaMemcpyAsync(dx + (size_t)first(i) * xpt, hx + (size_t)first(i) * xpt, (size_t)count(i) * xpt,
+                              cudaMemcpyHostToDevice, cs));
+      EFGP_CK(cudaEventRecord(ex[i], cs));
+    }
+    for (int i = 0; i < nch; ++i) {
+      EFGP_CK(cudaMemcpyAsync(dy + (size_t)first(i) * ypt, hy + (size_t)first(i) * ypt, (size_t)count(i) * ypt,
+                              cudaMemcpyHostToDevice, cs));
+      EFGP_CK(cudaEventRecord(ey[i], cs));
+    }
+    return EFGP_OK;
+  }
+  int wait_all() {
+    for (int i = 0; i < nch; ++i) EFGP_TRY(wait_y(i));
+    if (nch) EFGP_TRY(wait_x(nch - 1));
+    return EFGP_OK;
+  }
+};
+
 int free_temps(efgp_handle* H, std::vector<void*>& temps) {
   for (void* t : temps) cudaFreeAsync(t, H->stream);
   temps.clear();
@@ -636,7 +724,15 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   } guard{H, &temps};
 
   const void *dx, *dy;
-  EFGP_TRY(stage_inputs(H, x, y, N, &dx, &dy, temps));
+  ChunkedStage cst;   // (destroyed before the guard frees the staging buffers)
+  const bool chunked = H->opt.host_io && H->opt.x_layout == 0 && N > 2 * kStageChunk;
+  if (chunked) {
+    EFGP_TRY(cst.start(H, x, y, N, temps));
+    dx = cst.dx;
+    dy = cst.dy;
+  } else {
+    EFGP_TRY(stage_inputs(H, x, y, N, &dx, &dy, temps));
+  }
 
   // ---- bin geometry
   SortGeom sg{};
@@ -668,6 +764,7 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   int fused_blocks_n = 0;
   size_t fused_smem = 0;
   if (fused_eligible(H, sg, dx, dy, &fused_blocks_n, &fused_smem)) {
+    if (chunked) EFGP_TRY(cst.wait_all());
     EFGP_TRY(setup_fused_path(H, dx, dy, sg, fused_blocks_n, fused_smem, temps, &P));
   } else {
   void *counts = nullptr, *toff = nullptr, *cursor = nullptr, *rec = nullptr, *E = nullptr;
@@ -686,11 +783,18 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
     EFGP_CK(cudaMallocAsync(&rec, recb * (size_t)sg.rstride * (d + 1), H->stream));
     temps.push_back(rec);
     H->mark(0);
-    if (d == 2 && !coord_f64 && !sf64 && !soa && reinterpret_cast<uintptr_t>(dx) % 16 == 0 &&
-        sg.ntiles <= kFusedMaxTiles)
-      EFGP_CK(launch_tile_totals_2d((const float*)dx, N, sg, (unsigned int*)counts, H->flag, H->stream));
-    else
-      EFGP_CK(launch_bin_count(dx, coord_f64, (int)sf64, soa, N, sg, (unsigned int*)counts, H->flag, H->stream));
+    // tile totals, chunk by chunk as the chunks of x arrive (host inputs)
+    const int nparts = chunked ? cst.nch : 1;
+    for (int i = 0; i < nparts; ++i) {
+      const void* xi = chunked ? cst.x_at(i) : dx;
+      const long long ni = chunked ? cst.count(i) : N;
+      if (chunked) EFGP_TRY(cst.wait_x(i));
+      if (d == 2 && !coord_f64 && !sf64 && !soa && reinterpret_cast<uintptr_t>(xi) % 16 == 0 &&
+          sg.ntiles <= kFusedMaxTiles)
+        EFGP_CK(launch_tile_totals_2d((const float*)xi, ni, sg, (unsigned int*)counts, H->flag, H->stream));
+      else
+        EFGP_CK(launch_bin_count(xi, coord_f64, (int)sf64, soa, ni, sg, (unsigned int*)counts, H->flag, H->stream));
+    }
     H->mark(1);
     EFGP_CK(cudaMemcpyAsync(H->host_flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
     EFGP_CK(cudaStreamSynchronize(H->stream));
@@ -700,12 +804,18 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
     }
     H->mark(2);
     EFGP_CK(launch_scan_tiles((unsigned int*)counts, sg.ntiles, (long long*)toff, (long long*)cursor, H->stream));
-    EFGP_CK(launch_bin_scatter(dx, coord_f64, dy, value_f64, soa, N, sg, (int)sf64, (long long*)cursor, rec,
-                               H->flag + 1, H->stream));
+    // sorting scatter (global tile cursors: chunks may go in any order), chunk
+    // by chunk as the chunks of y arrive (host inputs)
+    for (int i = 0; i < nparts; ++i) {
+      if (chunked) EFGP_TRY(cst.wait_y(i));
+      EFGP_CK(launch_bin_scatter(chunked ? cst.x_at(i) : dx, coord_f64, chunked ? cst.y_at(i) : dy, value_f64, soa,
+                                 chunked ? cst.count(i) : N, sg, (int)sf64, (long long*)cursor, rec, H->flag + 1,
+                                 H->stream));
+    }
     H->mark(3);
     const void* coef = sf64 ? (const void*)&H->c1d : (const void*)&H->c1f;
     EFGP_CK(launch_spread(rec, (int)sf64, N, sg, (const long long*)toff, coef, (double2*)E, H->flag + 1, H->stream));
-    H->times.launches += 4;
+    H->times.launches += 2 * nparts + 2;
   }
   H->mark(4);
 

@@ -131,3 +131,37 @@ def test_se3d_clustered_full_size_sampled_parity(E):
     ref_mu = O.mean_at(zall[zi], beta, D, hh, m).real
     err = np.abs(mu - ref_mu).max()
     assert err <= 10 * eps * np.abs(yh).max(), (err, 10 * eps * np.abs(yh).max())
+
+
+def test_host_inputs_staged_in_chunks_match_device_inputs(E):
+    """Host inputs above two copy chunks (2^26 points each) are copied on a
+    second stream chunk by chunk, the tile count and the sorting scatter of
+    each chunk starting as soon as it has arrived: the result must match the
+    set-up from device arrays (FP32 in-tile sums in another order only)."""
+    name = "matern2d_1e9"
+    n = (1 << 27) + (1 << 25) + 12345          # three chunks, the last one partial
+    rec = synthdata.config(name, n=n)
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    x, y = synthdata.make_torch(rec, "cuda")
+    z = torch.from_numpy(synthdata.targets_np(rec)[:20000]).cuda()
+    kern = E.Kernel(fam, nu, ell)
+    hd = E.setup(x, y, kern, sigma, eps)
+    hd.solve()
+    mu_d = hd.predict(z).double().cpu().numpy()
+    wd, bd = hd.system()
+    hd.close()
+    xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    yh = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+    xh.copy_(x)
+    yh.copy_(y)
+    del x, y
+    torch.cuda.empty_cache()
+    hh = E.setup(xh.numpy(), yh.numpy(), kern, sigma, eps)
+    hh.solve()
+    mu_h = hh.predict(z.cpu().numpy())
+    wh, bh = hh.system()
+    hh.close()
+    tol = eps / 10
+    assert np.abs(wd - wh).max() / n <= 1e-2 * tol
+    assert np.abs(bd - bh).max() / float(np.abs(yh.numpy()).sum(dtype=np.float64)) <= 1e-2 * tol
+    assert np.abs(mu_d - mu_h).max() <= 0.2 * 10 * eps * float(np.abs(yh.numpy()).max())
