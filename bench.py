@@ -221,6 +221,11 @@ def cpu_sample_size(name):
 # products and CG run in FP64 (mixed_cg64).
 DEFAULT_PRECISION = {"se1d": "fp64", "matern2d_table4": "mixed_cg64"}
 
+# Jacobi-preconditioned CG where it was measured to pay on these workloads
+# (the 2D Matern ones: 4-40x fewer iterations at N = 1e6-1e9, means within
+# the criterion at full size); the 3D SE workload takes more iterations with it.
+DEFAULT_PRECOND = {"matern2d": 1, "matern2d_1e9": 1, "matern2d_table4": 1, "matern2d_table5": 1}
+
 # The paper's total run times (set-up, solve and the mean on the 1000^2 target
 # grid) for the exact N = 1e9 workloads of Sec. 5.4, on its 12-core desktop:
 # Table 4 (l = 0.1, sigma = 0.1, eps = 1e-5, m = 94) and Table 5 (same with
@@ -264,7 +269,8 @@ def setup_roofline(rec, d, coord_b, val_b, rec_bytes, tot, hbm, src, traffic_jso
 _DIRECT_CACHE = {}
 
 
-def accuracy_record(E, x, y, z, kern, sigma, eps, prec, name, setup_path=0, max_dense_M=12000, n_targets=2000):
+def accuracy_record(E, x, y, z, kern, sigma, eps, prec, name, setup_path=0, max_dense_M=12000, n_targets=2000,
+                    precond=0):
     """Mean error of the GPU path, the way tests/test_gpu_full_size.py checks it
     (CPU test infrastructure, outside any timed region): sampled entries of w
     (eq. 88) and b (eq. rhs) against FP64 direct sums over all points; then
@@ -272,7 +278,7 @@ def accuracy_record(E, x, y, z, kern, sigma, eps, prec, name, setup_path=0, max_
     sampled targets against the GPU's CG + type-2 mean, relative to max|y|."""
     import numpy as np
     from oracle import efgp_oracle as O
-    h = E.setup(x, y, kern, sigma, eps, precision=prec, setup_path=setup_path)
+    h = E.setup(x, y, kern, sigma, eps, precision=prec, setup_path=setup_path, precond=precond)
     info = h.solve()
     mu = h.predict(z).double().cpu().numpy()
     w, b = h.system()
@@ -332,13 +338,13 @@ def oracle_single_core(name, n_sample, q_sample):
     return v, dt
 
 
-def time_variant(E, x, y, z, kern, sigma, eps, prec, setup_path, steps, warmup=1):
+def time_variant(E, x, y, z, kern, sigma, eps, prec, setup_path, steps, warmup=1, precond=0):
     """ms per whole step (set-up, solve, predict) of another form of the path
     on the same device inputs, CUDA events on the current stream."""
     import torch
 
     def one():
-        h = E.setup(x, y, kern, sigma, eps, precision=prec, setup_path=setup_path, profile=1)
+        h = E.setup(x, y, kern, sigma, eps, precision=prec, setup_path=setup_path, profile=1, precond=precond)
         info = h.solve()
         h.predict(z)
         pt = h.phase_times()
@@ -540,6 +546,7 @@ def run_ours(args, rank, world):
     fam, nu, ell, sigma, eps = model
     kern = E.Kernel(fam, nu, ell)
     prec = args.precision or DEFAULT_PRECISION.get(name, "mixed")
+    precond = args.precond if args.precond >= 0 else DEFAULT_PRECOND.get(name, 0)
 
     if rec.cluster_frac > 0:       # clustered recipes are drawn on the host
         xn, yn = synthdata.points_np(rec), None
@@ -554,7 +561,7 @@ def run_ours(args, rank, world):
 
     def step(profile=0):
         h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile, cg_mode=args.cg_mode,
-                    autotune=args.autotune, setup_path=args.setup_path)
+                    autotune=args.autotune, setup_path=args.setup_path, precond=precond)
         info = h.solve()
         mu = h.predict(z)
         pt = h.phase_times()
@@ -612,11 +619,12 @@ def run_ours(args, rank, world):
     variants = {}
     if not args.no_variants:
         if d == 2 and prec != "fp64" and rec.coord_dtype == "float32":
-            ms_f, it_f, ph_f = time_variant(E, x, y, z, kern, sigma, eps, prec, 2, max(1, min(args.steps, 3)))
+            ms_f, it_f, ph_f = time_variant(E, x, y, z, kern, sigma, eps, prec, 2, max(1, min(args.steps, 3)),
+                                            precond=precond)
             variants["fused_deterministic_setup"] = {"ms_per_step": ms_f, "value": job_throughput(rec.n, world, ms_f),
                                                      "cg_iters": it_f, "phase_ms": ph_f}
         if prec != "fp64":
-            ms_d, it_d, ph_d = time_variant(E, x, y, z, kern, sigma, eps, "fp64", 0, 2)
+            ms_d, it_d, ph_d = time_variant(E, x, y, z, kern, sigma, eps, "fp64", 0, 2, precond=precond)
             variants["fp64_form"] = {"ms_per_step": ms_d, "value": job_throughput(rec.n, world, ms_d),
                                      "cg_iters": it_d, "phase_ms": ph_d}
 
@@ -630,7 +638,7 @@ def run_ours(args, rank, world):
     # posterior mean at all N training points (type-2 with q = N)
     at_data = None
     if args.at_data:
-        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=1)
+        h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=1, precond=precond)
         h.solve()
         mu_all = torch.empty(rec.n, dtype=y.dtype, device=dev)
         h.predict(x, out=mu_all)
@@ -653,9 +661,10 @@ def run_ours(args, rank, world):
     # accuracy of the measured form (and of the FP64 form), by the CPU
     # reference leg's procedure: outside every timed region, rank 0 at N = 1
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_accuracy:
-        accuracy = accuracy_record(E, x, y, z, kern, sigma, eps, prec, name)
+        accuracy = accuracy_record(E, x, y, z, kern, sigma, eps, prec, name, precond=precond)
         if "fp64_form" in variants:
-            variants["fp64_form"]["accuracy"] = accuracy_record(E, x, y, z, kern, sigma, eps, "fp64", name)
+            variants["fp64_form"]["accuracy"] = accuracy_record(E, x, y, z, kern, sigma, eps, "fp64", name,
+                                                                precond=precond)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -673,7 +682,7 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
 
         def e2e_step():
-            h = E.setup(xn, yn, kern, sigma, eps, precision=prec)
+            h = E.setup(xn, yn, kern, sigma, eps, precision=prec, precond=precond)
             h.solve()
             h.predict(zn, out=mu_h)
             h.close()
@@ -716,7 +725,8 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": paper_ratio(name, rec.n, value), "dtype": "f64" if prec == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": workload_desc(name, rec, model), "precision": prec, "m": par["m"],
+            "config": {"workload": workload_desc(name, rec, model), "precision": prec, "precond": precond,
+                       "m": par["m"],
                        "M": par["M"], "L": par["L"], "nf1": par["nf1"], "w1": par["w1"], "nf2": par["nf2"],
                        "w2": par["w2"], "l2_flush": "inputs larger than L2 (%.1f GB)" % (
                            rec.n * (d * coord_b + val_b) / 1e9), "parallelism": f"independent problem per GPU x{world}"},
@@ -759,6 +769,8 @@ def main():
                     help="time candidate line batches per Toeplitz pass before the CG graph is captured")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="CG launch form (0 chooses; see efgp_options.cg_mode)")
+    ap.add_argument("--precond", type=int, default=-1, choices=[-1, 0, 1],
+                    help="Jacobi-preconditioned CG (efgp_options.precond; -1: the workload's default)")
     ap.add_argument("--setup-path", type=int, default=0, choices=[0, 1, 2],
                     help="set-up kernels (0 chooses; 1 three passes; 2 fused chunked; see efgp_options.setup_path)")
     ap.add_argument("--at-data", action="store_true",

@@ -79,8 +79,8 @@ typedef struct {
   int value_dtype;      /* dtype of y and mu_out (efgp_dtype)                              */
   int x_layout;         /* 0: row-major N x d; 1: structure of arrays d x N               */
   int host_io;          /* 0: device pointers; 1: host pointers, copied by the library    */
-  double cg_tol;        /* relative residual rho (0: eps/10; the Algorithm's step 4 uses  */
-                        /* rho ~ eps, see efgp_solve)                                      */
+  double cg_tol;        /* relative residual rho (0: the default of efgp_solve; the       */
+                        /* Algorithm's step 4 uses rho ~ eps)                              */
   int64_t max_iter;     /* CG iteration cap (0: 100000)                                   */
   double nufft_tol;     /* NUFFT accuracy (0: eps/10, Sec. 5.1)                           */
   int m_override;       /* > 0: use this m instead of the Sec. 4.2 choice                 */
@@ -107,6 +107,12 @@ typedef struct {
                         /* bitwise reproducible, compensated FP64 tile sums (2D, FP32 x */
                         /* and y, row-major, 16-byte aligned, mixed precision; other    */
                         /* problems take the three passes)                              */
+  int precond;          /* 1: Jacobi-preconditioned CG, M = diag(A) = D_j^2 w_0 + sigma^2  */
+                        /* (Sec. 6 leaves preconditioning open); the stopping rule stays  */
+                        /* ||r|| <= rho ||b|| with a default rho ten times smaller (a     */
+                        /* preconditioned iterate's mean error at a given residual is     */
+                        /* larger; see efgp_solve).                                        */
+                        /* Graph-captured CG only (cg_mode 0 or 1; else EUNSUPPORTED)     */
 } efgp_options;
 
 /* Discretisation and NUFFT parameters chosen for a problem. */
@@ -177,11 +183,15 @@ int efgp_setup(const void* x, const void* y, int64_t N, int d, const efgp_kernel
 
 /* Step 4: conjugate gradients on (D F^*F D + sigma^2 I) beta = D F^* y
  * (eqs. 97, be) from beta = 0, stopping at ||r||/||b|| <= rho or max_iter.
- * The default rho is eps/10, one digit below the paper's rho ~ eps, so that
- * the posterior mean stays within 10 eps max|y| of the exact solution of the
- * same discretised system (with rho = eps that error reaches 15-25 eps max|y|).
- * info may be NULL.  Returns ENOTCONV if max_iter was reached (beta is then
- * the last iterate and predict still works). */
+ * The default rho is eps/10 * min(1, sqrt(1e7 / kappa)) with
+ * kappa = 1 + N D_0^2 / sigma^2 (D_0^2 = h^d khat(0)), divided by a further 10
+ * with the Jacobi preconditioner: one or more digits below the paper's
+ * rho ~ eps, so that the posterior mean stays within 10 eps max|y| of the
+ * exact solution of the same discretised system (measured at N = 1e9: with
+ * rho = eps that error reaches 15-25 eps max|y| at kappa ~ 4e7, and rho =
+ * eps/10 leaves 44 eps max|y| at kappa ~ 2e9).  info may be NULL.  Returns
+ * ENOTCONV if max_iter was reached (beta is then the last iterate and
+ * predict still works). */
 int efgp_solve(efgp_handle* h, efgp_solve_info* info);
 
 /* Step 6: mu(z_i) = sum_j D_j beta_j exp(2 pi i h j.z_i) for q targets in

@@ -24,7 +24,8 @@ class efgp_options(C.Structure):
                 ("m_override", C.c_int), ("h_override", C.c_double), ("fft_len_override", C.c_int),
                 ("upsampfac", C.c_double), ("es_width", C.c_int), ("iters_per_launch", C.c_int),
                 ("autotune", C.c_int), ("profile", C.c_int), ("cg_mode", C.c_int),
-                ("stream", C.c_void_p), ("setup_path", C.c_int)]
+                ("stream", C.c_void_p), ("setup_path", C.c_int),
+                ("precond", C.c_int)]
 
 
 class efgp_params(C.Structure):

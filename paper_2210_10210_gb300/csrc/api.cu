@@ -270,6 +270,25 @@ void pinned_put(char* p) {
 // max|y|, while eps/10 keeps them below 10 eps max|y|.
 double default_rho(double eps) { return eps / 10.0; }
 
+// Default stopping residual of a handle.  How much mean error a residual
+// leaves grows with the conditioning of D W D + sigma^2 I, estimated by
+// kappa = 1 + N D_0^2 / sigma^2 (D_0^2 = h^d khat(0), the largest weight, and
+// w_0 = N); measured against the exact solution at N = 1e9 (2D Matern-3/2):
+// kappa ~ 4e7 (l = 0.05, sigma = 0.5) keeps eps/10 within 10 eps max|y|
+// (2.2 eps), kappa ~ 2e9 (l = 0.1, sigma = 0.1) needs ~eps/100 (44 eps at
+// eps/10, 5.9 at eps/100).  So rho = eps/10 * min(1, sqrt(1e7 / kappa)).
+// With the Jacobi preconditioner the same residual leaves about ten times the
+// mean error (10.3 vs 2.2 eps, and 37 vs 5.9), so its rho is ten times smaller.
+double solve_rho(const efgp_handle* H) {
+  const double h = H->par.h;
+  const double hd = H->d == 1 ? h : (H->d == 2 ? h * h : h * h * h);
+  const double d0sq = hd * kernel_spectral_density(H->kern, H->d, 0.0);   // (variance included)
+  const double kappa = 1.0 + (double)H->N * d0sq / (H->sigma * H->sigma);
+  double rho = default_rho(H->eps) * std::min(1.0, std::sqrt(1e7 / kappa));
+  if (H->opt.precond) rho /= 10.0;
+  return rho;
+}
+
 
 }  // namespace
 
@@ -1004,6 +1023,7 @@ int capture_cg_graph(efgp_handle* H) {
   cga.sigma2 = H->sigma * H->sigma;
   cga.st = H->st;
   cga.partials = H->partials;
+  cga.Minv = H->Minv;
   cga.update_p = 1;
   cga.do_dot = 1;
   cga.check_done = 1;
@@ -1013,7 +1033,7 @@ int capture_cg_graph(efgp_handle* H) {
   for (int it = 0; it < iters && rc == EFGP_OK; ++it) {
     rc = run_passes(H, H->mvg, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
     if (rc == EFGP_OK) {
-      cudaError_t e = launch_cg_update(H->x, H->r, H->p, H->Ap, H->M, H->st, H->partials, H->stream);
+      cudaError_t e = launch_cg_update(H->x, H->r, H->p, H->Ap, H->M, H->st, H->partials, H->Minv, H->stream);
       if (e != cudaSuccess) {
         set_error(std::string("cg update: ") + cudaGetErrorString(e));
         rc = EFGP_ECUDA;
@@ -1527,7 +1547,20 @@ int efgp_setup(const void* x, const void* y, int64_t N, int d, const efgp_kernel
 
 int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   if (!H) return EFGP_EINVAL;
-  const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
+  const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : solve_rho(H);
+  if (H->opt.precond) {
+    // Jacobi preconditioner: the graph-captured CG only
+    if (H->opt.cg_mode != 0 && H->opt.cg_mode != 1) {
+      set_error("precond = 1 needs cg_mode 0 or 1 (graph-captured CG)");
+      return EFGP_EUNSUPPORTED;
+    }
+    if (!H->Minv) {
+      EFGP_TRY(H->alloc((void**)&H->Minv, sizeof(double) * H->M));
+      const long long k4 = ipow(4 * H->par.m + 1, H->d);
+      EFGP_CK(launch_jacobi(H->Dw, H->w + k4 / 2, H->sigma * H->sigma, H->M, H->Minv, H->stream));
+      H->times.launches += 1;
+    }
+  }
   const long long max_iter = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
   const bool queued = H->opt.cg_mode == 3;
   bool persistent = false, grid = false;
@@ -1562,7 +1595,7 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
     EFGP_CK(cudaMemcpyAsync(H->host_state, H->st, sizeof(CgState), cudaMemcpyDeviceToHost, H->stream));
     EFGP_CK(cudaStreamSynchronize(H->stream));
   } else {
-  EFGP_CK(launch_cg_init(H->b, H->x, H->r, H->p, H->M, rho, max_iter, H->st, H->partials, H->stream));
+  EFGP_CK(launch_cg_init(H->b, H->x, H->r, H->p, H->M, rho, max_iter, H->st, H->partials, H->Minv, H->stream));
   H->times.launches += 1;
   long long launched = 0;
   while (true) {
@@ -1951,7 +1984,7 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
       cga.check_done = 1;
       for (int it = 0; it < iters && rc == EFGP_OK; ++it) {
         rc = run_passes(H, H->mvg, nullptr, H->scrA, H->scrB, H->what, H->twL, &cga);
-        if (rc == EFGP_OK && launch_cg_update(H->x, H->r, H->p, H->Ap, H->M, H->st, H->partials, H->stream) !=
+        if (rc == EFGP_OK && launch_cg_update(H->x, H->r, H->p, H->Ap, H->M, H->st, H->partials, H->Minv, H->stream) !=
                                  cudaSuccess)
           rc = EFGP_ECUDA;
       }
@@ -1977,7 +2010,7 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
   for (efgp_handle* H : B->hs) {
     const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
     const long long mi = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
-    EFGP_CK(launch_cg_init(H->b, H->x, H->r, H->p, H->M, rho, mi, H->st, H->partials, B->main));
+    EFGP_CK(launch_cg_init(H->b, H->x, H->r, H->p, H->M, rho, mi, H->st, H->partials, H->Minv, B->main));
   }
   long long launched = 0;
   while (true) {

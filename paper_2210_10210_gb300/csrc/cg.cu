@@ -20,23 +20,36 @@ int cg_blocks(long long M) {
   return (int)b;
 }
 
+// Sums of two values over the block (results valid in thread 0).
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+  a = block_sum(a, red);
+  __syncthreads();
+  b = block_sum(b, red);
+}
+
+// x = 0, r = b, p = z = M^-1 r (z = r without a preconditioner); ||b||^2 and
+// r^H z reduced in block order by the last block.
 __global__ void __launch_bounds__(kCgThreads) cg_init_kernel(const double2* __restrict__ b, double2* __restrict__ x,
                                                              double2* __restrict__ r, double2* __restrict__ p,
                                                              long long M, double rho, long long max_iter, CgState* st,
-                                                             double* partials) {
+                                                             double* partials, const double* __restrict__ Minv) {
   __shared__ double red[32];
-  double s = 0.0;
+  double s = 0.0, sz = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double2 v = b[i];
+    const double mi = Minv ? Minv[i] : 1.0;
     x[i] = make_double2(0.0, 0.0);
     r[i] = v;
-    p[i] = v;
-    s += v.x * v.x + v.y * v.y;
+    p[i] = make_double2(mi * v.x, mi * v.y);
+    const double n2 = v.x * v.x + v.y * v.y;
+    s += n2;
+    sz += mi * n2;
   }
-  const double bs = block_sum(s, red);
+  block_sum2(s, sz, red);
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = bs;
+    partials[blockIdx.x] = s;
+    partials[gridDim.x + blockIdx.x] = sz;
     __threadfence();
     last = (atomicAdd(&st->ticket_b, 1u) == gridDim.x - 1);
   }
@@ -44,9 +57,12 @@ __global__ void __launch_bounds__(kCgThreads) cg_init_kernel(const double2* __re
   if (last) {
     __threadfence();
     const double tot = block_sum_partials(partials, gridDim.x, red);
+    __syncthreads();
+    const double totz = block_sum_partials(partials + gridDim.x, gridDim.x, red);
     if (threadIdx.x == 0) {
       st->bnorm2 = tot;
       st->rr = tot;
+      st->rz = Minv ? totz : tot;
       st->rr_new = tot;
       st->tol2 = rho * rho * tot;
       st->iter = 0;
@@ -60,15 +76,18 @@ __global__ void __launch_bounds__(kCgThreads) cg_init_kernel(const double2* __re
   }
 }
 
+// x += alpha p, r -= alpha A p; r^H r (the stopping rule) and r^H M^-1 r (for
+// beta = (r^H z)_new / (r^H z)) reduced in block order by the last block.
 __global__ void __launch_bounds__(kCgThreads) cg_update_kernel(double2* __restrict__ x, double2* __restrict__ r,
                                                                const double2* __restrict__ p,
                                                                const double2* __restrict__ Ap, long long M,
-                                                               CgState* st, double* partials) {
+                                                               CgState* st, double* partials,
+                                                               const double* __restrict__ Minv) {
   __shared__ double red[32];
   grid_dependency_wait();
   if (st->done) return;
   const double alpha = st->alpha;
-  double s = 0.0;
+  double s = 0.0, sz = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double2 pv = p[i], av = Ap[i];
     double2 xv = x[i], rv = r[i];
@@ -78,12 +97,16 @@ __global__ void __launch_bounds__(kCgThreads) cg_update_kernel(double2* __restri
     rv.y -= alpha * av.y;
     x[i] = xv;
     r[i] = rv;
-    s += rv.x * rv.x + rv.y * rv.y;
+    const double n2 = rv.x * rv.x + rv.y * rv.y;
+    s += n2;
+    if (Minv) sz += Minv[i] * n2;
   }
-  const double bs = block_sum(s, red);
+  if (Minv) block_sum2(s, sz, red);
+  else s = block_sum(s, red);
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = bs;
+    partials[blockIdx.x] = s;
+    if (Minv) partials[gridDim.x + blockIdx.x] = sz;
     __threadfence();
     last = (atomicAdd(&st->ticket_b, 1u) == gridDim.x - 1);
   }
@@ -91,17 +114,30 @@ __global__ void __launch_bounds__(kCgThreads) cg_update_kernel(double2* __restri
   if (last) {
     __threadfence();
     const double tot = block_sum_partials(partials, gridDim.x, red);
+    double totz = tot;
+    if (Minv) {
+      __syncthreads();
+      totz = block_sum_partials(partials + gridDim.x, gridDim.x, red);
+    }
     if (threadIdx.x == 0) {
       st->rr_new = tot;
       st->iter += 1;
-      st->beta = tot / st->rr;
+      st->beta = totz / st->rz;
       st->rr = tot;
+      st->rz = totz;
       if (!isfinite(tot)) st->done = 3;
       else if (tot <= st->tol2) st->done = 1;
       else if (st->iter >= st->max_iter) st->done = 2;
       st->ticket_b = 0u;
     }
   }
+}
+
+__global__ void jacobi_kernel(const double* __restrict__ Dw, const double2* __restrict__ wc, double sigma2,
+                              long long M, double* __restrict__ Minv) {
+  const double w0 = wc->x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x)
+    Minv[i] = 1.0 / (Dw[i] * Dw[i] * w0 + sigma2);
 }
 
 // out_sum[0] = ||b - Ax||^2 (single value, deterministic)
@@ -135,14 +171,20 @@ __global__ void __launch_bounds__(kCgThreads) residual_kernel(const double2* __r
 }
 
 cudaError_t launch_cg_init(const double2* b, double2* x, double2* r, double2* p, long long M, double rho,
-                           long long max_iter, CgState* st, double* partials, cudaStream_t s) {
-  cg_init_kernel<<<cg_blocks(M), kCgThreads, 0, s>>>(b, x, r, p, M, rho, max_iter, st, partials);
+                           long long max_iter, CgState* st, double* partials, const double* Minv, cudaStream_t s) {
+  cg_init_kernel<<<cg_blocks(M), kCgThreads, 0, s>>>(b, x, r, p, M, rho, max_iter, st, partials, Minv);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update(double2* x, double2* r, const double2* p, const double2* Ap, long long M, CgState* st,
-                             double* partials, cudaStream_t s) {
-  return launch_pdl(cg_update_kernel, dim3(cg_blocks(M)), dim3(kCgThreads), 0, s, x, r, p, Ap, M, st, partials);
+                             double* partials, const double* Minv, cudaStream_t s) {
+  return launch_pdl(cg_update_kernel, dim3(cg_blocks(M)), dim3(kCgThreads), 0, s, x, r, p, Ap, M, st, partials, Minv);
+}
+
+cudaError_t launch_jacobi(const double* Dw, const double2* w_center, double sigma2, long long M, double* Minv,
+                          cudaStream_t s) {
+  jacobi_kernel<<<cg_blocks(M), kCgThreads, 0, s>>>(Dw, w_center, sigma2, M, Minv);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_residual_norm(const double2* b, const double2* Ax, long long M, double* out_sum, double* partials,

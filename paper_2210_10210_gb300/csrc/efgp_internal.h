@@ -89,6 +89,7 @@ struct alignas(16) EsCoef {
 
 struct CgState {
   double rr;          // r^H r
+  double rz;          // r^H M^-1 r (= rr without a preconditioner)
   double rr_new;
   double pAp;
   double alpha;

@@ -45,7 +45,7 @@ __device__ void pap_reduce(double dot, const CgArgs& cga, double* red) {
         st->alpha = 0.0;
         st->done = 3;   // breakdown: p^H A p not positive
       } else {
-        st->alpha = st->rr / tot;
+        st->alpha = st->rz / tot;
       }
       st->ticket_a = 0u;
     }
@@ -102,7 +102,12 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_fwd_kernel(LineGeom g, in
       const long long j = base + (long long)j1 * n1 + k;
       double2 pv = __ldcg(cga.src + j);
       if (cga.update_p) {
-        const double2 rv = __ldcg(cga.r + j);
+        double2 rv = __ldcg(cga.r + j);
+        if (cga.Minv) {
+          const double mi = cga.Minv[j];
+          rv.x *= mi;
+          rv.y *= mi;
+        }
         pv.x = rv.x + beta * pv.x;
         pv.y = rv.y + beta * pv.y;
         cga.src[j] = pv;

@@ -61,6 +61,7 @@ struct efgp_handle {
   double2 *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
   CgState* st = nullptr;
   double* partials = nullptr;
+  double* Minv = nullptr;   // Jacobi preconditioner (options.precond)
   void* scrA = nullptr;
   void* scrB = nullptr;
   void* g2 = nullptr;

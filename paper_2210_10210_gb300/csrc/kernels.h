@@ -17,6 +17,7 @@ struct CgArgs {
   double sigma2;         // sigma^2
   CgState* st;           // CG scalars (may be null outside CG)
   double* partials;      // per-block partial dot products
+  const double* Minv;    // Jacobi preconditioner 1 / diag(A) (M), or null (plain CG)
   int update_p;          // 1: first pass sets src = r + beta*src (iteration > 0)
   int do_dot;            // 1: last pass reduces Re(src^H dst) into st->pAp, alpha
   int check_done;        // 1: skip everything once st->done is set
@@ -134,10 +135,14 @@ cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, size_t smem, cudaStream_t 
 }
 
 // ---- CG vector kernels (cg.cu)
+// Minv: the Jacobi preconditioner 1 / diag(A), or null for plain CG.
 cudaError_t launch_cg_init(const double2* b, double2* x, double2* r, double2* p, long long M, double rho,
-                           long long max_iter, CgState* st, double* partials, cudaStream_t s);
+                           long long max_iter, CgState* st, double* partials, const double* Minv, cudaStream_t s);
 cudaError_t launch_cg_update(double2* x, double2* r, const double2* p, const double2* Ap, long long M, CgState* st,
-                             double* partials, cudaStream_t s);
+                             double* partials, const double* Minv, cudaStream_t s);
+// Minv_j = 1 / (D_j^2 Re w_0 + sigma^2): the diagonal of D W D + sigma^2 I
+cudaError_t launch_jacobi(const double* Dw, const double2* w_center, double sigma2, long long M, double* Minv,
+                          cudaStream_t s);
 cudaError_t launch_residual_norm(const double2* b, const double2* Ax, long long M, double* out_sum, double* partials,
                                  unsigned int* ticket, cudaStream_t s);
 int cg_blocks(long long M);

@@ -265,7 +265,12 @@ __device__ double line_block(const LineGeom& g, long long blk, const void* __res
         const long long j = base + k;   // flat index into the M-vector
         double2 pv = __ldcg(cga.src + j);
         if (cga.update_p) {
-          const double2 rv = __ldcg(cga.r + j);
+          double2 rv = __ldcg(cga.r + j);
+          if (cga.Minv) {   // preconditioned residual z = M^-1 r
+            const double mi = cga.Minv[j];
+            rv.x *= mi;
+            rv.y *= mi;
+          }
           pv.x = rv.x + cg_beta * pv.x;
           pv.y = rv.y + cg_beta * pv.y;
           cga.src[j] = pv;

@@ -121,3 +121,44 @@ def test_sixty_four_problem_batch(E):
             checked += 1
     B.close()
     assert checked >= 5
+
+
+@pytest.mark.parametrize("name,n,precision", [("matern2d", 100_000, "mixed"), ("se3d", 100_000, "mixed"),
+                                              ("matern2d_table5", 100_000, "fp64"),
+                                              ("matern2d_table4", 100_000, "mixed_cg64")])
+def test_jacobi_preconditioned_cg(E, name, n, precision):
+    """Jacobi-preconditioned CG (options.precond = 1, M = diag(A)) with its
+    default stop ||r|| <= (eps/100) ||b||: the mean must meet the same
+    criterion against the reference (the oracle, or at m = 94 the exact-sum
+    reference above); the iteration counts of both forms are printed."""
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    if name.startswith("matern2d_table"):
+        x, y, z, h, m, D, w, b, mu_ref = _reference(name, n, 3000)
+    else:
+        rec = synthdata.config(name, n=n)
+        x, y, z = synthdata.make_np(rec)
+        z = z[:3000]
+        mu_ref = O.efgp(x, y, z, O.Kernel(fam, nu, ell), sigma, eps).mu
+    its = {}
+    for pc in (0, 1):
+        h = E.setup(_dev(x), _dev(y), E.Kernel(fam, nu, ell), sigma, eps, precision=precision, precond=pc)
+        info = h.solve()
+        mu = h.predict(_dev(z)).double().cpu().numpy()
+        h.close()
+        assert info["converged"] and info["true_rel_residual"] <= 10 * eps, (pc, info)
+        its[pc] = info["iters"]
+        err = np.abs(mu - mu_ref).max()
+        assert err <= 10 * eps * np.abs(y).max(), (pc, err, 10 * eps * np.abs(y).max())
+    print(f"{name}: CG iterations plain {its[0]}, Jacobi {its[1]}")
+
+
+def test_preconditioner_needs_graph_cg(E):
+    from paper_2210_10210_gb300 import _capi
+    rec = synthdata.config("matern2d", n=5000)
+    x, y, _ = synthdata.make_np(rec)
+    fam, nu, ell, sigma, eps = synthdata.MODELS["matern2d"]
+    h = E.setup(_dev(x), _dev(y), E.Kernel(fam, nu, ell), sigma, eps, precond=1, cg_mode=3)
+    with pytest.raises(E.EfgpError) as ei:
+        h.solve()
+    assert ei.value.status == _capi.EFGP_EUNSUPPORTED
+    h.close()
