@@ -561,7 +561,8 @@ def run_ours(args, rank, world):
 
     def step(profile=0):
         h = E.setup(x, y, kern, sigma, eps, precision=prec, profile=profile, cg_mode=args.cg_mode,
-                    autotune=args.autotune, setup_path=args.setup_path, precond=precond)
+                    autotune=args.autotune, setup_path=args.setup_path, precond=precond,
+                    cg_tol=args.cg_tol or None)
         info = h.solve()
         mu = h.predict(z)
         pt = h.phase_times()
@@ -726,6 +727,7 @@ def run_ours(args, rank, world):
             "vs_baseline": paper_ratio(name, rec.n, value), "dtype": "f64" if prec == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(name, rec, model), "precision": prec, "precond": precond,
+                       "cg_tol": args.cg_tol or "default",
                        "m": par["m"],
                        "M": par["M"], "L": par["L"], "nf1": par["nf1"], "w1": par["w1"], "nf2": par["nf2"],
                        "w2": par["w2"], "l2_flush": "inputs larger than L2 (%.1f GB)" % (
@@ -769,6 +771,8 @@ def main():
                     help="time candidate line batches per Toeplitz pass before the CG graph is captured")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="CG launch form (0 chooses; see efgp_options.cg_mode)")
+    ap.add_argument("--cg-tol", type=float, default=0.0,
+                    help="CG stopping residual rho (0: the library's default)")
     ap.add_argument("--precond", type=int, default=-1, choices=[-1, 0, 1],
                     help="Jacobi-preconditioned CG (efgp_options.precond; -1: the workload's default)")
     ap.add_argument("--setup-path", type=int, default=0, choices=[0, 1, 2],

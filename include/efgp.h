@@ -154,6 +154,8 @@ typedef struct {
   int64_t n_setup, n_solve, n_predict;  /* calls timed                           */
   int64_t launches;      /* kernels this handle has launched (graph nodes count)  */
   int64_t cg_iters;      /* CG iterations run                                     */
+  int64_t setups_fused;  /* set-ups that took the fused chunked kernels (the rest */
+                         /* took the three passes; see efgp_options.setup_path)   */
 } efgp_phase_times;
 
 typedef struct efgp_handle efgp_handle;

@@ -49,7 +49,7 @@ class efgp_phase_times(C.Structure):
                 ("fine_fft_ms", C.c_double), ("what_ms", C.c_double), ("cg_ms", C.c_double),
                 ("predict_fft_ms", C.c_double), ("interp_ms", C.c_double), ("n_setup", C.c_int64),
                 ("n_solve", C.c_int64), ("n_predict", C.c_int64), ("launches", C.c_int64),
-                ("cg_iters", C.c_int64)]
+                ("cg_iters", C.c_int64), ("setups_fused", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -723,6 +723,7 @@ int setup_fused_path(efgp_handle* H, const void* dx, const void* dy, const SortG
   EFGP_CK(cudaMemcpyAsync(H->flag + 2, &((GridBarrier*)gb)->err, sizeof(int), cudaMemcpyDeviceToDevice, H->stream));
   H->mark(4);
   H->times.launches += 4;
+  H->times.setups_fused += 1;
   *P_out = P;
   return EFGP_OK;
 }

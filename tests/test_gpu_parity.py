@@ -258,16 +258,23 @@ def test_cg_iteration_cap_reports_not_converged(E):
     assert torch.isfinite(mu).all()
 
 
+# The fused set-up applies to ES widths <= 6: the planner picks them for the
+# billion-point workload (sigma_up = 2.5, W = 5), at small N it prefers wider
+# kernels on smaller grids; the fused-path tests fix that plan.
+_FUSED_PLAN = dict(upsampfac=2.5, es_width=5)
+
+
 def test_deterministic_rerun(E):
     """The fused set-up sums in an order fixed by the input alone (stable
     counting sorts, slot reductions in block order) and the CG reduces in
     block order: two runs give bitwise-identical w, b, beta and mean."""
-    rec = synthdata.config("matern2d", n=300_000)
+    rec = synthdata.config("matern2d_1e9", n=300_000)
     x, y, z = synthdata.make_np(rec)
-    ek, _, sigma, eps = _kernel(E, synthdata.MODELS["matern2d"])
+    ek, _, sigma, eps = _kernel(E, synthdata.MODELS["matern2d_1e9"])
     outs = []
     for _ in range(2):
-        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=2)
+        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=2, **_FUSED_PLAN)
+        assert h.phase_times()["setups_fused"] == 1
         h.solve()
         w, b = h.system()
         outs.append((w, b, h.beta(), h.predict(_dev(z[:2000])).cpu().numpy()))
@@ -289,7 +296,8 @@ def test_fused_setup_matches_three_pass(E, n):
     ek, _, sigma, eps = _kernel(E, synthdata.MODELS["matern2d_1e9"])
     got = {}
     for path in (1, 2):
-        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=path)
+        h = E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=path, **_FUSED_PLAN)
+        assert h.phase_times()["setups_fused"] == (1 if path == 2 and n > 0 else 0)
         got[path] = h.system()
         h.close()
     tol = eps / 10
@@ -535,3 +543,23 @@ def test_device_apply_matches_host_apply(E):
     torch.cuda.synchronize()
     h.close()
     assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_fused_setup_bounded_barrier_wait_reports_timeout(E, monkeypatch):
+    """EFGP_FAULT=setup_stall presets the fused set-up's grid barrier with
+    more arrivals than blocks: every block's bounded wait runs out after
+    the chunk's scatter, the launch returns, the host reports EFGP_ETIMEOUT,
+    and a new set-up then works."""
+    from paper_2210_10210_gb300 import _capi
+    rec = synthdata.config("matern2d_1e9", n=50_000)
+    x, y, z = synthdata.make_np(rec)
+    ek, ok, sigma, eps = _kernel(E, synthdata.MODELS["matern2d_1e9"])
+    monkeypatch.setenv("EFGP_FAULT", "setup_stall")
+    with pytest.raises(E.EfgpError) as ei:
+        E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=2, **_FUSED_PLAN)
+    assert ei.value.status == _capi.EFGP_ETIMEOUT
+    monkeypatch.delenv("EFGP_FAULT")
+    h = E.setup(_dev(x), _dev(y), ek, sigma, eps, setup_path=2, **_FUSED_PLAN)
+    assert h.phase_times()["setups_fused"] == 1
+    assert h.solve()["converged"]
+    h.close()
