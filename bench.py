@@ -224,7 +224,7 @@ DEFAULT_PRECISION = {"se1d": "fp64", "matern2d_table4": "mixed_cg64"}
 # Jacobi-preconditioned CG where it was measured to pay on these workloads
 # (the 2D Matern ones: 4-40x fewer iterations at N = 1e6-1e9, means within
 # the criterion at full size); the 3D SE workload takes more iterations with it.
-DEFAULT_PRECOND = {"matern2d": 1, "matern2d_1e9": 1, "matern2d_table4": 1, "matern2d_table5": 1}
+DEFAULT_PRECOND = {"matern2d": 1, "matern2d_1e9": 1, "matern2d_table4": 1, "matern2d_table5": 1, "batch": 1}
 
 # The paper's total run times (set-up, solve and the mean on the 1000^2 target
 # grid) for the exact N = 1e9 workloads of Sec. 5.4, on its 12-core desktop:
@@ -408,6 +408,7 @@ def run_batch(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    precond = args.precond if args.precond >= 0 else DEFAULT_PRECOND.get("batch", 0)
     probs = synthdata.batch_problems(seed=6 + 1000 * rank, count=args.batch_count)
     items, targets, npts = [], [], 0
     for rec, model in probs:
@@ -419,7 +420,8 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
 
     def step():
-        B = E.batch_setup(items, precision=args.precision or "mixed", cg_mode=args.cg_mode, autotune=args.autotune)
+        B = E.batch_setup(items, precision=args.precision or "mixed", cg_mode=args.cg_mode, autotune=args.autotune,
+                          precond=precond)
         infos = B.solve()
         for i in range(len(items)):
             B.predict(i, targets[i])
@@ -454,7 +456,7 @@ def run_batch(args, rank, world):
             "cg_iters_max": max(iters), "cg_iters_median": sorted(iters)[len(iters) // 2],
             "cg_iters_total": sum(iters), "cg_ms": sum(solve_ms) / len(solve_ms), "cg_mode": args.cg_mode,
             "cg_iters_per_s": sum(iters) / (sum(solve_ms) / len(solve_ms) / 1000),
-            "precision": args.precision or "mixed",
+            "precision": args.precision or "mixed", "precond": precond,
             "clocks": clk.summary(),
         }), flush=True)
     if dist:

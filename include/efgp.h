@@ -111,8 +111,8 @@ typedef struct {
                         /* (Sec. 6 leaves preconditioning open); the stopping rule stays  */
                         /* ||r|| <= rho ||b|| with a default rho ten times smaller (a     */
                         /* preconditioned iterate's mean error at a given residual is     */
-                        /* larger; see efgp_solve).                                        */
-                        /* Graph-captured CG only (cg_mode 0 or 1; else EUNSUPPORTED)     */
+                        /* larger; see efgp_solve).  Graph-captured and scheduled CG    */
+                        /* (cg_mode 0, 1 or 3; cg_mode 2 or 4 gives EUNSUPPORTED)         */
 } efgp_options;
 
 /* Discretisation and NUFFT parameters chosen for a problem. */

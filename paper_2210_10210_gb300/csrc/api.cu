@@ -289,6 +289,16 @@ double solve_rho(const efgp_handle* H) {
   return rho;
 }
 
+// The Jacobi preconditioner of a handle (options.precond), built once.
+int prepare_precond(efgp_handle* H) {
+  if (!H->opt.precond || H->Minv) return EFGP_OK;
+  EFGP_TRY(H->alloc((void**)&H->Minv, sizeof(double) * H->M));
+  const long long k4 = ipow(4 * H->par.m + 1, H->d);
+  EFGP_CK(launch_jacobi(H->Dw, H->w + k4 / 2, H->sigma * H->sigma, H->M, H->Minv, H->stream));
+  H->times.launches += 1;
+  return EFGP_OK;
+}
+
 
 }  // namespace
 
@@ -1278,12 +1288,15 @@ int queue_prepare(efgp_handle* H, double rho, long long max_iter, int resident, 
   P.st = H->st;
   P.rho = rho;
   P.max_iter = max_iter;
+  P.Minv = H->Minv;
   if (H->qpartials_n < maxitems) {
-    EFGP_TRY(H->alloc((void**)&H->qpartials, sizeof(double) * maxitems));
+    // (second half: the r^H z sums of the preconditioned form)
+    EFGP_TRY(H->alloc((void**)&H->qpartials, sizeof(double) * 2 * maxitems));
     H->qpartials_n = maxitems;
   }
   if (!H->qctl) EFGP_TRY(H->alloc((void**)&H->qctl, sizeof(QueueCtl)));
   Q.partials = H->qpartials;
+  Q.partials2 = H->Minv ? H->qpartials + H->qpartials_n : nullptr;
   Q.ctl = H->qctl;
   *out = Q;
   *smem = std::max(*smem, sm);
@@ -1550,17 +1563,12 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
   if (!H) return EFGP_EINVAL;
   const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : solve_rho(H);
   if (H->opt.precond) {
-    // Jacobi preconditioner: the graph-captured CG only
-    if (H->opt.cg_mode != 0 && H->opt.cg_mode != 1) {
-      set_error("precond = 1 needs cg_mode 0 or 1 (graph-captured CG)");
+    // Jacobi preconditioner: graph-captured and scheduled CG
+    if (H->opt.cg_mode == 2 || H->opt.cg_mode == 4) {
+      set_error("precond = 1 needs cg_mode 0, 1 or 3 (graph-captured or scheduled CG)");
       return EFGP_EUNSUPPORTED;
     }
-    if (!H->Minv) {
-      EFGP_TRY(H->alloc((void**)&H->Minv, sizeof(double) * H->M));
-      const long long k4 = ipow(4 * H->par.m + 1, H->d);
-      EFGP_CK(launch_jacobi(H->Dw, H->w + k4 / 2, H->sigma * H->sigma, H->M, H->Minv, H->stream));
-      H->times.launches += 1;
-    }
+    EFGP_TRY(prepare_precond(H));
   }
   const long long max_iter = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
   const bool queued = H->opt.cg_mode == 3;
@@ -1871,8 +1879,9 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
       const int resident = resident_queue_blocks(B->hs[0]->f64);
       for (int i = 0; i < n; ++i) {
         efgp_handle* H = B->hs[i];
-        const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
+        const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : solve_rho(H);
         const long long mi = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
+        EFGP_TRY(prepare_precond(H));
         EFGP_TRY(queue_prepare(H, rho, mi, resident, &qs[i], &smem));
         EFGP_CK(cudaStreamSynchronize(H->stream));
       }
@@ -1909,7 +1918,11 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
     int cl = 16, f64 = B->hs[0]->f64;
     size_t smem = 0;
     for (efgp_handle* H : B->hs) {
-      const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
+      if (H->opt.precond) {
+        set_error("precond = 1 needs cg_mode 0, 1 or 3 (graph-captured or scheduled CG)");
+        return EFGP_EUNSUPPORTED;
+      }
+      const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : solve_rho(H);
       const long long mi = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
       EFGP_TRY(persistent_prepare(H, rho, mi, true));
       all = all && H->pcluster > 0 && H->f64 == f64;
@@ -1963,6 +1976,11 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
   const int iters = B->hs[0]->opt.iters_per_launch > 0 ? B->hs[0]->opt.iters_per_launch : 32;
   long long max_iter = 0;
   for (efgp_handle* h : B->hs) max_iter = std::max<long long>(max_iter, h->opt.max_iter > 0 ? h->opt.max_iter : 100000);
+  for (efgp_handle* h : B->hs) {
+    // the preconditioners exist before the graph that reads them is captured
+    EFGP_TRY(prepare_precond(h));
+    EFGP_CK(cudaStreamSynchronize(h->stream));
+  }
   if (!B->graph) {
     // one graph: each problem's group of iterations on its own branch
     cudaEvent_t ev0 = B->ev[n];
@@ -1980,6 +1998,7 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
       cga.sigma2 = H->sigma * H->sigma;
       cga.st = H->st;
       cga.partials = H->partials;
+      cga.Minv = H->Minv;
       cga.update_p = 1;
       cga.do_dot = 1;
       cga.check_done = 1;
@@ -2009,7 +2028,7 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
   cudaEvent_t e0 = evp.a, e1 = evp.b;
   EFGP_CK(cudaEventRecord(e0, B->main));
   for (efgp_handle* H : B->hs) {
-    const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : default_rho(H->eps);
+    const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : solve_rho(H);
     const long long mi = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
     EFGP_CK(launch_cg_init(H->b, H->x, H->r, H->p, H->M, rho, mi, H->st, H->partials, H->Minv, B->main));
   }

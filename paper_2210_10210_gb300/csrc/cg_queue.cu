@@ -60,22 +60,29 @@ __device__ __forceinline__ void publish(unsigned long long* w, unsigned long lon
 }
 
 // Runs item `item` of phase `ph`; returns this thread's part of the phase's sum.
+// With the Jacobi preconditioner the init and update items also return
+// their part of r^H M^-1 r in *s2.
 template <typename T>
-__device__ double run_item(const QueueProblem& Q, int ph, unsigned item, unsigned char* smem) {
+__device__ double run_item(const QueueProblem& Q, int ph, unsigned item, unsigned char* smem, double* s2) {
   const PersistentProblem& P = Q.P;
   const volatile QueueCtl* c = Q.ctl;
+  *s2 = 0.0;
   if (ph == 0 || ph == P.npass + 1) {
     const long long i0 = (long long)item * kQueueChunk;
     const long long i1 = min(P.M, i0 + kQueueChunk);
-    double s = 0.0;
+    double s = 0.0, sz = 0.0;
     if (ph == 0) {
       for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const double2 v = __ldcg(P.b + i);
+        const double mi = P.Minv ? P.Minv[i] : 1.0;
         P.x[i] = make_double2(0.0, 0.0);
         P.r[i] = v;
-        P.p[i] = v;
-        s += v.x * v.x + v.y * v.y;
+        P.p[i] = make_double2(mi * v.x, mi * v.y);
+        const double n2 = v.x * v.x + v.y * v.y;
+        s += n2;
+        sz += mi * n2;
       }
+      *s2 = sz;
     } else {
       const double alpha = c->alpha;
       for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
@@ -87,12 +94,16 @@ __device__ double run_item(const QueueProblem& Q, int ph, unsigned item, unsigne
         rv.y -= alpha * av.y;
         P.x[i] = xv;
         P.r[i] = rv;
-        s += rv.x * rv.x + rv.y * rv.y;
+        const double n2 = rv.x * rv.x + rv.y * rv.y;
+        s += n2;
+        if (P.Minv) sz += P.Minv[i] * n2;
       }
+      *s2 = sz;
     }
     return s;
   }
   CgArgs cga{};
+  cga.Minv = P.Minv;
   cga.src = P.p;
   cga.r = P.r;
   cga.Dw = P.Dw;
@@ -104,7 +115,7 @@ __device__ double run_item(const QueueProblem& Q, int ph, unsigned item, unsigne
 
 // The block that finished phase `ph` (sequence number seq) of problem Q, with
 // the phase's total `tot`: CG scalars, then the next phase or the end.
-__device__ void advance(const QueueProblem& Q, unsigned seq, int ph, double tot, unsigned int* ndone) {
+__device__ void advance(const QueueProblem& Q, unsigned seq, int ph, double tot, double tot2, unsigned int* ndone) {
   volatile QueueCtl* c = Q.ctl;
   const PersistentProblem& P = Q.P;
   int done = 0;
@@ -112,6 +123,7 @@ __device__ void advance(const QueueProblem& Q, unsigned seq, int ph, double tot,
     c->bnorm2 = tot;
     c->tol2 = P.rho * P.rho * tot;
     c->rr = tot;
+    c->rz = P.Minv ? tot2 : tot;
     c->it = 0;
     c->alpha = 0.0;
     c->beta = 0.0;
@@ -121,12 +133,14 @@ __device__ void advance(const QueueProblem& Q, unsigned seq, int ph, double tot,
   } else if (ph == P.npass) {
     c->pAp = tot;
     if (!(tot > 0.0) || !isfinite(tot)) done = 3;   // breakdown: p^H A p not positive
-    else c->alpha = c->rr / tot;
+    else c->alpha = c->rz / tot;
   } else if (ph == P.npass + 1) {
     const long long it = c->it + 1;
     c->it = it;
-    c->beta = tot / c->rr;
+    const double rz = P.Minv ? tot2 : tot;
+    c->beta = rz / c->rz;
     c->rr = tot;
+    c->rz = rz;
     if (!isfinite(tot)) done = 3;
     else if (tot <= c->tol2) done = 1;
     else if (it >= P.max_iter) done = 2;
@@ -224,20 +238,31 @@ __global__ void __launch_bounds__(kQueueThreads, sizeof(T) == 4 ? 2 : 1) cg_queu
     const unsigned seq = s_seq, item = s_item;
     const int npass = Q.P.npass;
     const int ph = phase_of(seq, npass);
-    const double part = run_item<T>(Q, ph, item, smem_raw);
+    double part2 = 0.0;
+    const double part = run_item<T>(Q, ph, item, smem_raw, &part2);
     const bool reduce = ph == 0 || ph == npass || ph == npass + 1;
-    double bs = 0.0;
+    const bool reduce2 = Q.P.Minv && (ph == 0 || ph == npass + 1);
+    double bs = 0.0, bs2 = 0.0;
     if (reduce) bs = block_sum(part, red);
+    if (reduce2) {
+      __syncthreads();
+      bs2 = block_sum(part2, red);
+    }
     if (tid == 0) {
       if (reduce) Q.partials[item] = bs;
+      if (reduce2) Q.partials2[item] = bs2;
       const unsigned done_items = complete_add(&Q.ctl->completed);
       s_last = done_items == (unsigned)Q.items[ph] - 1;
     }
     __syncthreads();
     if (s_last) {
-      double tot = 0.0;
+      double tot = 0.0, tot2 = 0.0;
       if (reduce) tot = block_sum_partials(Q.partials, Q.items[ph], red);
-      if (tid == 0) advance(Q, seq, ph, tot, ndone);
+      if (reduce2) {
+        __syncthreads();
+        tot2 = block_sum_partials(Q.partials2, Q.items[ph], red);
+      }
+      if (tid == 0) advance(Q, seq, ph, tot, tot2, ndone);
     }
     __syncthreads();
   }

@@ -71,6 +71,7 @@ struct PersistentProblem {
   double rho;
   long long max_iter;
   CgState* st;           // final state written here
+  const double* Minv;    // Jacobi preconditioner (scheduled CG), or null
 };
 cudaError_t launch_cg_persistent(const PersistentProblem* d_probs, int nprob, int cluster, size_t smem, int f64,
                                  cudaStream_t s);
@@ -101,11 +102,13 @@ struct alignas(128) QueueCtl {
   int done;                  // 0 running, 1 converged, 2 iteration cap, 3 breakdown
   double rr, alpha, beta, bnorm2, tol2, pAp;
   long long it;
+  double rz;                 // r^H M^-1 r (= rr without a preconditioner)
 };
 struct QueueProblem {
   PersistentProblem P;           // passes (line batches chosen for this kernel), buffers, scalars
   int items[kMaxPasses + 2];     // work items of phase 0 (init), 1..npass (passes), npass+1 (update)
   double* partials;              // one partial sum per item of the largest phase
+  double* partials2;             // second sums of the init and update items (r^H z), or null
   QueueCtl* ctl;
 };
 // aux[0]: problems finished, aux[1]: error flags (host zeroes both and every

@@ -99,6 +99,13 @@ def test_sixty_four_problem_batch(E):
     B = E.batch_setup(items)
     infos = B.solve()
     assert all(i["converged"] for i in infos)
+    # the same batch with the Jacobi preconditioner (one scheduled launch)
+    Bp = E.batch_setup(items, precond=1)
+    infos_p = Bp.solve()
+    assert all(i["converged"] for i in infos_p)
+    print("batch CG iterations: plain max %d sum %d, Jacobi max %d sum %d" % (
+        max(i["iters"] for i in infos), sum(i["iters"] for i in infos),
+        max(i["iters"] for i in infos_p), sum(i["iters"] for i in infos_p)))
     checked = 0
     for i, (x, y, z, model) in enumerate(cases):
         fam, nu, ell, sigma, eps = model
@@ -115,11 +122,17 @@ def test_sixty_four_problem_batch(E):
         # mean: they agree to half of it
         assert abs(i1["iters"] - infos[i]["iters"]) <= max(5, 0.2 * i1["iters"]), (i, i1, infos[i])
         assert np.abs(mu - mu1).max() <= 0.5 * scale, i
+        mu_p = Bp.predict(i, _dev(z)).double().cpu().numpy()
+        # the preconditioned iterate may sit up to the criterion from the
+        # exact mean (reading 17), the plain one within half of it
+        assert np.abs(mu_p - mu1).max() <= scale, i
         if par["M"] <= 12000 and x.shape[0] <= 100_000:
             ref = O.efgp(x, y, z, O.Kernel(fam, nu, ell), sigma, eps)
             assert np.abs(mu - ref.mu).max() <= scale, i
+            assert np.abs(mu_p - ref.mu).max() <= scale, i
             checked += 1
     B.close()
+    Bp.close()
     assert checked >= 5
 
 
@@ -152,13 +165,34 @@ def test_jacobi_preconditioned_cg(E, name, n, precision):
     print(f"{name}: CG iterations plain {its[0]}, Jacobi {its[1]}")
 
 
-def test_preconditioner_needs_graph_cg(E):
+def test_preconditioner_needs_graph_or_scheduled_cg(E):
     from paper_2210_10210_gb300 import _capi
     rec = synthdata.config("matern2d", n=5000)
     x, y, _ = synthdata.make_np(rec)
     fam, nu, ell, sigma, eps = synthdata.MODELS["matern2d"]
-    h = E.setup(_dev(x), _dev(y), E.Kernel(fam, nu, ell), sigma, eps, precond=1, cg_mode=3)
-    with pytest.raises(E.EfgpError) as ei:
-        h.solve()
-    assert ei.value.status == _capi.EFGP_EUNSUPPORTED
-    h.close()
+    for mode in (2, 4):
+        h = E.setup(_dev(x), _dev(y), E.Kernel(fam, nu, ell), sigma, eps, precond=1, cg_mode=mode)
+        with pytest.raises(E.EfgpError) as ei:
+            h.solve()
+        assert ei.value.status == _capi.EFGP_EUNSUPPORTED
+        h.close()
+
+
+@pytest.mark.parametrize("name,n", [("matern2d", 100_000), ("se3d", 50_000)])
+def test_preconditioned_scheduled_cg_matches_graph(E, name, n):
+    """The Jacobi preconditioner in the scheduled (work-claiming) CG kernel
+    against the graph-captured preconditioned CG: same iterations up to
+    rounding, same mean."""
+    rec = synthdata.config(name, n=n)
+    x, y, z = synthdata.make_np(rec)
+    z = z[:3000]
+    fam, nu, ell, sigma, eps = synthdata.MODELS[name]
+    out = {}
+    for mode in (1, 3):
+        h = E.setup(_dev(x), _dev(y), E.Kernel(fam, nu, ell), sigma, eps, precond=1, cg_mode=mode)
+        info = h.solve()
+        assert info["converged"] and info["true_rel_residual"] <= 10 * eps, (mode, info)
+        out[mode] = (info["iters"], h.predict(_dev(z)).double().cpu().numpy())
+        h.close()
+    assert abs(out[1][0] - out[3][0]) <= max(5, 0.1 * out[1][0])
+    assert np.abs(out[1][1] - out[3][1]).max() <= 0.2 * 10 * eps * np.abs(y).max()

@@ -115,6 +115,25 @@ def test_se_choice_meets_uniform_bound(d, ell, eps):
     assert err.max() <= eps
 
 
+@pytest.mark.parametrize("d,eps,h_hand,m_hand", [(1, 1e-4, 0.6740, 12), (2, 1e-4, 0.6582, 13), (3, 1e-3, 0.6650, 13)])
+def test_se_printed_formula_at_table2_configs(d, eps, h_hand, m_hand):
+    """The printed SE choice (Sec. 4.2) at Table 2's SE configurations
+    (l = 0.1), worked by hand.  Table 2 itself prints m = 13/16/17, which
+    this formula does not give (the uniform-bound pin above is the
+    one-sided check; the table's values are not reproduced).
+      d = 1, eps = 1e-4: log(4*1*3/eps) = log(1.2e5) = 11.695, sqrt(2*11.695)
+        = 4.836, h = 1/1.4836 = 0.6740; log(4^2*1/eps) = log(1.6e5) = 11.983,
+        sqrt(11.983/2) = 2.4478, / (pi*0.1*0.6740 = 0.21174) = 11.56 -> m = 12
+      d = 2, eps = 1e-4: log(72/eps) = 13.487, sqrt(26.975) = 5.1937,
+        h = 1/1.51937 = 0.6582; log(4^3*2/eps) = 14.062, sqrt(7.031) = 2.6516,
+        / (pi*0.1*0.6582 = 0.20677) = 12.82 -> m = 13
+      d = 3, eps = 1e-3: log(324/eps) = 12.688, sqrt(25.376) = 5.0374,
+        h = 1/1.50374 = 0.6650; log(4^4*3/eps) = 13.552, sqrt(6.776) = 2.6031,
+        / (pi*0.1*0.6650 = 0.20892) = 12.46 -> m = 13"""
+    h, m = O.choose_h_m(O.Kernel("se", 0.0, 0.1), d, eps)
+    assert abs(h - h_hand) < 5e-5 and m == m_hand
+
+
 @pytest.mark.parametrize("nu,d,ell,eps", [(3.5, 1, 0.1, 1e-6), (3.5, 2, 0.2, 1e-4), (4.5, 2, 0.1, 1e-3),
                                           (3.5, 3, 0.4, 1e-2)])
 def test_matern_high_nu_choice_meets_uniform_bound(nu, d, ell, eps):
