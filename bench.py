@@ -35,7 +35,7 @@ UNIT = "points/s"
 
 
 CSRC = os.path.join(ROOT, "paper_2210_10210_gb300", "csrc")
-KERNEL_NAMES = {"spread": ("spread.cu", "spread_tma_kernel("), "bin_scatter": ("spread.cu", "bin_scatter_tma_kernel("),
+KERNEL_NAMES = {"spread": ("spread.cu", "spread_tma_kernel("), "bin_scatter": ("spread.cu", "bin_scatter_big_kernel("),
                 "bin_count": ("setup_fused.cu", "fused_count_kernel(")}
 
 

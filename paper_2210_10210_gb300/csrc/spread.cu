@@ -404,6 +404,138 @@ __global__ void __launch_bounds__(kTmaScatterThreads, 1)
   if (abort_flag && tid == 0 && pending_other) mbar_wait_bounded(&bar[(it & 1) ^ 1], (uint32_t)(((it + 1) >> 1) & 1), err);
 }
 
+// Sorting scatter over 8192-point chunks (at most 1024 tiles): twice the
+// points of a chunk per tile run (longer write runs, half the cursor
+// reservations per point).  One staging buffer: each point's tile-local
+// coordinates overwrite its coordinates in place, the chunk is reordered into
+// a second buffer, and the next chunk's bulk copy is issued into the staging
+// buffer then, so it lands while the reordered chunk is written out.
+constexpr int kBigScatterPPT = 16;
+constexpr int kBigScatterChunk = kTmaScatterThreads * kBigScatterPPT;
+constexpr int kBigScatterMaxTiles = 1024;
+constexpr int kBigScatterMaxSlice = (kBigScatterMaxTiles + kTmaScatterThreads - 1) / kTmaScatterThreads;
+
+template <int D>
+__global__ void __launch_bounds__(kTmaScatterThreads, 1)
+    bin_scatter_big_kernel(const float* __restrict__ x, const float* __restrict__ y, long long nfull, SortGeom sg,
+                           long long* __restrict__ cursor, float* __restrict__ rec, int* err) {
+  constexpr int NT = kTmaScatterThreads, PPT = kBigScatterPPT, P = kBigScatterChunk;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int T = sg.ntiles;
+  float* stage = reinterpret_cast<float*>(smraw);                                  // (D+1) x P: x then y
+  float* sq = stage + (D + 1) * P;                                                  // (D+1) x P, sorted
+  unsigned short* stile = reinterpret_cast<unsigned short*>(sq + (D + 1) * P);     // P
+  long long* base = reinterpret_cast<long long*>(stile + P);                       // T
+  unsigned int* hist = reinterpret_cast<unsigned int*>(base + T);                  // T
+  int* lstart = reinterpret_cast<int*>(hist + T);                                  // T
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int wtot[NT / 32];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  const uint32_t bytes_x = D * P * 4, bytes_y = P * 4;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    abort_flag = 0;
+  }
+  __syncthreads();
+  long long c = blockIdx.x;
+  if (tid == 0 && c < nfull) {
+    mbar_arrive_expect_tx(&bar, bytes_x + bytes_y);
+    bulk_g2s(stage, x + c * (long long)P * D, bytes_x, &bar);
+    bulk_g2s(stage + D * P, y + c * (long long)P, bytes_y, &bar);
+  }
+  const int slice = (T + NT - 1) / NT;
+  uint32_t ph = 0u;
+  bool pending = c < nfull;
+  for (; c < nfull; c += gridDim.x) {
+    for (int i = tid; i < T; i += NT) hist[i] = 0u;
+    if (mbar_wait_bounded(&bar, ph, err)) {
+      ph ^= 1u;
+      pending = false;
+    } else {
+      abort_flag = 1;   // (the copy waited for is still in flight: pending)
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    int tt[PPT];
+    unsigned int rk[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const int k = p * NT + tid;
+      float xa[3];
+#pragma unroll
+      for (int a = 0; a < D; ++a) xa[a] = stage[k * D + a];
+      bool bad = false;
+      float q[3];
+      tt[p] = tile_of_coords<D, float, float>(xa, sg, q, bad);
+#pragma unroll
+      for (int a = 0; a < D; ++a) stage[k * D + a] = q[a];   // same thread, same slot
+      rk[p] = atomicAdd(&hist[tt[p]], 1u);
+    }
+    __syncthreads();
+    const int a0 = tid * slice, a1 = min(T, a0 + slice);
+    unsigned long long got[kBigScatterMaxSlice];
+    {
+      int sum = 0;
+      for (int i = a0; i < a1; ++i) sum += (int)hist[i];
+      int run = block_excl_scan_n<NT>(sum, wtot);
+#pragma unroll
+      for (int u = 0; u < kBigScatterMaxSlice; ++u) {
+        const int i = a0 + u;
+        got[u] = 0ull;
+        if (i < a1) {
+          lstart[i] = run;
+          const unsigned int h = hist[i];
+          run += (int)h;
+          if (h) got[u] = atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[i]), (unsigned long long)h);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      const int k = p * NT + tid;
+      const int pos = lstart[tt[p]] + (int)rk[p];
+#pragma unroll
+      for (int a = 0; a < D; ++a) sq[a * P + pos] = stage[k * D + a];
+      sq[D * P + pos] = stage[D * P + k];
+      stile[pos] = (unsigned short)tt[p];
+    }
+#pragma unroll
+    for (int u = 0; u < kBigScatterMaxSlice; ++u)
+      if (a0 + u < a1) base[a0 + u] = (long long)got[u];
+    __syncthreads();
+    // the staging buffer is free: the next chunk's copy lands during the write-out
+    const long long cn = c + gridDim.x;
+    if (cn < nfull) {
+      pending = true;
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar, bytes_x + bytes_y);
+        bulk_g2s(stage, x + cn * (long long)P * D, bytes_x, &bar);
+        bulk_g2s(stage + D * P, y + cn * (long long)P, bytes_y, &bar);
+      }
+    }
+    for (int i = tid; i < P; i += NT) {
+      const int t = stile[i];
+      const long long g = base[t] + (i - lstart[t]);
+#pragma unroll
+      for (int a = 0; a <= D; ++a) rec[(long long)a * sg.rstride + g] = sq[a * P + i];
+    }
+    __syncthreads();
+  }
+  // after an abandoned wait, let a copy already issued land (bounded) before
+  // the block's shared memory is released
+  if (abort_flag && tid == 0 && pending) mbar_wait_bounded(&bar, ph, err);
+}
+
+size_t scatter_big_smem(int d, int ntiles) {
+  const size_t P = kBigScatterChunk;
+  return sizeof(float) * (2 * (size_t)(d + 1) * P) + sizeof(unsigned short) * P +
+         (sizeof(long long) + 2 * sizeof(int)) * ntiles;
+}
+
 size_t scatter_tma_smem(int d, int ntiles) {
   const size_t P = kTmaScatterChunk;
   return sizeof(float) * (3 * (size_t)(d + 1) * P) + sizeof(int) * P + (sizeof(long long) + 2 * sizeof(int)) * ntiles;
@@ -1246,8 +1378,31 @@ static cudaError_t scatter_d(const void* x, const void* y, int soa, long long N,
   if (sg.ntiles <= kSortedScatterMaxTiles) {
     if constexpr (std::is_same<TC, float>::value && std::is_same<TV, float>::value &&
                   std::is_same<TR, float>::value) {
-      const size_t sm = scatter_tma_smem(D, sg.ntiles);
       const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) && (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+      const size_t smb = scatter_big_smem(D, sg.ntiles);
+      const long long nbig = N / kBigScatterChunk;
+      if (!soa && aligned && sg.ntiles <= kBigScatterMaxTiles && smb <= 226 * 1024 && nbig > 0) {
+        auto k = bin_scatter_big_kernel<D>;
+        cudaError_t e = allow_smem(k, smb);
+        if (e != cudaSuccess) {
+          set_error("bulk-copy scatter: shared-memory opt-in of " + std::to_string(smb) + " bytes failed: " +
+                    cudaGetErrorString(e));
+          return e;
+        }
+        const int blocks = (int)std::min<long long>(nbig, nsm);
+        k<<<blocks, kTmaScatterThreads, smb, s>>>(reinterpret_cast<const float*>(x), reinterpret_cast<const float*>(y),
+                                                  nbig, sg, cursor, reinterpret_cast<float*>(rec), err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+          set_error("bulk-copy scatter launch (" + std::to_string(blocks) + " blocks, " + std::to_string(smb) +
+                    " bytes): " + cudaGetErrorString(e));
+          return e;
+        }
+        const long long done = nbig * kBigScatterChunk;
+        if (done < N) return scatter_sorted<D, TC, TV, TR>(x, y, soa, N, done, sg, cursor, rec, nsm, s);
+        return cudaSuccess;
+      }
+      const size_t sm = scatter_tma_smem(D, sg.ntiles);
       const long long nfull = N / kTmaScatterChunk;
       if (!soa && aligned && sm <= 226 * 1024 && nfull > 0) {
         auto k = bin_scatter_tma_kernel<D>;
