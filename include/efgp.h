@@ -89,9 +89,10 @@ typedef struct {
   double upsampfac;     /* > 0: NUFFT fine-grid upsampling factor (else chosen)           */
   int es_width;         /* > 0: ES kernel width in grid points (else chosen)              */
   int iters_per_launch; /* CG iterations per captured CUDA graph launch (0: 32)           */
-  int autotune;         /* 1: before the CG graph is captured, time each line pass of the  */
-                        /* product at a few line batches and thread counts (once per pass */
-                        /* shape and precision in the process) and keep the fastest      */
+  int autotune;         /* 1: before the first solve, time each line pass of the Toeplitz  */
+                        /* product at a few line batches, thread counts and orders of its */
+                        /* Stockham radices (once per pass shape and precision in the     */
+                        /* process) and keep the fastest, for every CG form              */
   int profile;          /* 1: time each phase with CUDA events (efgp_get_phase_times)     */
   int cg_mode;          /* 0: choose (one problem: 1; a batch: 3);                      */
                         /* 1: graph-captured kernels per iteration;                        */

@@ -944,9 +944,32 @@ struct TuneKey {
   }
 };
 
+// Candidate orders of a line's Stockham radices (any order gives the same
+// DFT): the default (descending), ascending, and each distinct radix first
+// with the rest descending.
+std::vector<std::vector<int>> radix_orders(const LineGeom& g) {
+  std::vector<int> base(g.radix, g.radix + g.npass);
+  std::vector<std::vector<int>> out{base};
+  std::vector<int> asc(base.rbegin(), base.rend());
+  out.push_back(asc);
+  for (int i = 0; i < g.npass; ++i) {
+    std::vector<int> v = base;
+    std::rotate(v.begin(), v.begin() + i, v.begin() + i + 1);
+    out.push_back(v);
+  }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+  return out;
+}
+
+struct TuneChoice {
+  int nb, threads;
+  std::vector<int> radix;
+};
+
 int autotune_passes(efgp_handle* H, std::vector<Pass>& ps) {
   static std::mutex mu;
-  static std::map<TuneKey, std::pair<int, int>> tuned;   // -> (lines per block, threads)
+  static std::map<TuneKey, TuneChoice> tuned;   // -> lines per block, threads, radix order
   CgArgs cga{};
   cga.src = H->p;
   cga.r = H->r;
@@ -966,23 +989,29 @@ int autotune_passes(efgp_handle* H, std::vector<Pass>& ps) {
       std::lock_guard<std::mutex> lk(mu);
       auto it = tuned.find(key);
       if (it != tuned.end()) {
-        p.g.nb = it->second.first;
-        p.threads = it->second.second;
+        p.g.nb = it->second.nb;
+        p.threads = it->second.threads;
+        for (int i = 0; i < p.g.npass; ++i) p.g.radix[i] = it->second.radix[i];
         continue;
       }
     }
-    std::vector<std::pair<int, int>> cands;
-    for (int nb : {p.g.nb, std::max(1, p.g.nb / 2), std::min(kMaxLineBatch, 2 * p.g.nb)})
-      for (int th : {256, 512})
-        if (line_fft_smem_bytes(p.g.L, nb, H->elem) <= (size_t)kLineFftMaxSmem &&
-            std::find(cands.begin(), cands.end(), std::make_pair(nb, th)) == cands.end())
-          cands.push_back({nb, th});
+    std::vector<TuneChoice> cands;
+    const std::vector<std::vector<int>> orders = radix_orders(p.g);
+    for (const auto& ro : orders)
+      for (int nb : {p.g.nb, std::max(1, p.g.nb / 2), std::min(kMaxLineBatch, 2 * p.g.nb)})
+        for (int th : {256, 512}) {
+          if (line_fft_smem_bytes(p.g.L, nb, H->elem) > (size_t)kLineFftMaxSmem) continue;
+          bool dup = false;
+          for (const auto& c : cands) dup = dup || (c.nb == nb && c.threads == th && c.radix == ro);
+          if (!dup) cands.push_back(TuneChoice{nb, th, ro});
+        }
     float best = 1e30f;
-    std::pair<int, int> pick{p.g.nb, p.threads};
+    TuneChoice pick{p.g.nb, p.threads, std::vector<int>(p.g.radix, p.g.radix + p.g.npass)};
     for (const auto& c : cands) {
       Pass t = p;
-      t.g.nb = c.first;
-      t.threads = c.second;
+      t.g.nb = c.nb;
+      t.threads = c.threads;
+      for (int i = 0; i < t.g.npass; ++i) t.g.radix[i] = c.radix[i];
       auto launch = [&]() -> cudaError_t {
         if (H->f64)
           return launch_line_fft<double>(t.g, bufs[t.in_buf], bufs[t.out_buf], t.dir,
@@ -1014,17 +1043,29 @@ int autotune_passes(efgp_handle* H, std::vector<Pass>& ps) {
       }
     }
     if (rc != EFGP_OK) break;
-    p.g.nb = pick.first;
-    p.threads = pick.second;
+    p.g.nb = pick.nb;
+    p.threads = pick.threads;
+    for (int i = 0; i < p.g.npass; ++i) p.g.radix[i] = pick.radix[i];
     std::lock_guard<std::mutex> lk(mu);
     tuned[key] = pick;
   }
   return rc;
 }
 
+// options.autotune: the Toeplitz passes of every CG form (the graph-captured
+// product and the line passes the persistent and scheduled kernels use),
+// tuned once per handle (choices cached per pass shape in the process).
+int tune_once(efgp_handle* H) {
+  if (!H->opt.autotune || H->tuned) return EFGP_OK;
+  EFGP_TRY(autotune_passes(H, H->mvg));
+  EFGP_TRY(autotune_passes(H, H->mv));
+  H->tuned = true;
+  return EFGP_OK;
+}
+
 int capture_cg_graph(efgp_handle* H) {
   if (H->graph) return EFGP_OK;
-  if (H->opt.autotune) EFGP_TRY(autotune_passes(H, H->mvg));
+  EFGP_TRY(tune_once(H));
   const int iters = H->opt.iters_per_launch > 0 ? H->opt.iters_per_launch : 32;
   CgArgs cga{};
   cga.src = H->p;
@@ -1571,6 +1612,7 @@ int efgp_solve(efgp_handle* H, efgp_solve_info* info) {
     EFGP_TRY(prepare_precond(H));
   }
   const long long max_iter = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
+  EFGP_TRY(tune_once(H));
   const bool queued = H->opt.cg_mode == 3;
   bool persistent = false, grid = false;
   if (H->opt.cg_mode == 4) {
@@ -1882,6 +1924,7 @@ int efgp_batch_solve(efgp_batch* B, efgp_solve_info* info) {
         const double rho = H->opt.cg_tol > 0 ? H->opt.cg_tol : solve_rho(H);
         const long long mi = H->opt.max_iter > 0 ? H->opt.max_iter : 100000;
         EFGP_TRY(prepare_precond(H));
+        EFGP_TRY(tune_once(H));
         EFGP_TRY(queue_prepare(H, rho, mi, resident, &qs[i], &smem));
         EFGP_CK(cudaStreamSynchronize(H->stream));
       }

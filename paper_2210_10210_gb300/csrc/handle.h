@@ -81,6 +81,7 @@ struct efgp_handle {
   EsCoef<float> c1f{}, c2f{};
   EsCoef<double> c1d{}, c2d{};
   bool solved = false;
+  bool tuned = false;       // options.autotune applied to the Toeplitz passes
   std::vector<void*> allocs;
   efgp_phase_times times{};
   // persistent CG (one launch on a thread-block cluster)
