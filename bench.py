@@ -616,6 +616,39 @@ def run_ours(args, rank, world):
     val_b = 4 if rec.value_dtype == "float32" else 8
     roofline = setup_roofline(rec, d, coord_b, val_b, rec_bytes, tot, hbm, src, args.traffic_json)
 
+    # end to end through the C ABI from pinned host buffers (first after the
+    # timed region: the cuFFT baseline's plans and graphs slow later copies)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        yh = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+        zh = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
+        xh.copy_(x)
+        yh.copy_(y)
+        zh.copy_(z)
+        xn, yn, zn = xh.numpy(), yh.numpy(), zh.numpy()
+        mu_h = torch.empty(q, dtype=torch.float32 if rec.value_dtype == "float32" else torch.float64,
+                           pin_memory=True).numpy()
+
+        def e2e_step():
+            h = E.setup(xn, yn, kern, sigma, eps, precision=prec, precond=precond)
+            h.solve()
+            h.predict(zn, out=mu_h)
+            h.close()
+
+        for _ in range(max(2, args.warmup)):     # the device pool grows on the first steps
+            e2e_step()
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = max_over_ranks((time.perf_counter() - t0) / ke, dist, dev)
+        e2e = {"value": job_throughput(rec.n, world, 1000 * te), "unit": UNIT,
+               "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes + zn.nbytes), "d2h_bytes_per_step": int(mu_h.nbytes),
+               "ms_per_step": 1000 * te}
+
     accuracy = None
     # other forms of the same step, outside the timed region: the bitwise
     # reproducible fused set-up, and the plain FP64 form (precision pattern)
@@ -660,38 +693,6 @@ def run_ours(args, rank, world):
                    "interp_gbs": ib / (ims / 1000) / 1e9, "interp_frac_hbm": ib / (ims / 1000) / 1e9 / hbm,
                    "alg_bytes": ib}
         del mu_all
-
-    # end to end through the C ABI from pinned host buffers
-    e2e = None
-    if not args.no_e2e:
-        xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-        yh = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
-        zh = torch.empty(z.shape, dtype=z.dtype, pin_memory=True)
-        xh.copy_(x)
-        yh.copy_(y)
-        zh.copy_(z)
-        xn, yn, zn = xh.numpy(), yh.numpy(), zh.numpy()
-        mu_h = torch.empty(q, dtype=torch.float32 if rec.value_dtype == "float32" else torch.float64,
-                           pin_memory=True).numpy()
-
-        def e2e_step():
-            h = E.setup(xn, yn, kern, sigma, eps, precision=prec, precond=precond)
-            h.solve()
-            h.predict(zn, out=mu_h)
-            h.close()
-
-        for _ in range(max(2, args.warmup)):     # the device pool grows on the first steps
-            e2e_step()
-        torch.cuda.synchronize()
-        ke = max(1, min(args.steps, 3))
-        t0 = time.perf_counter()
-        for _ in range(ke):
-            e2e_step()
-        torch.cuda.synchronize()
-        te = max_over_ranks((time.perf_counter() - t0) / ke, dist, dev)
-        e2e = {"value": job_throughput(rec.n, world, 1000 * te), "unit": UNIT,
-               "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes + zn.nbytes), "d2h_bytes_per_step": int(mu_h.nbytes),
-               "ms_per_step": 1000 * te}
 
     # accuracy of the measured form (and of the FP64 form), by the CPU
     # reference leg's procedure: outside every timed region, rank 0 at N = 1,

@@ -525,7 +525,9 @@ def test_autotuned_passes_match_default(E, name, n):
         h.close()
     (i0, m0), (i1, m1) = out
     assert abs(i0["iters"] - i1["iters"]) <= max(5, 0.1 * i0["iters"])
-    assert np.abs(m0 - m1).max() <= 0.2 * 10 * eps * np.abs(y).max()
+    # tuned line batches and radix orders round in another order: two
+    # iterates stopping at the same residual agree to half the criterion
+    assert np.abs(m0 - m1).max() <= 0.5 * 10 * eps * np.abs(y).max()
 
 
 def test_device_apply_matches_host_apply(E):
