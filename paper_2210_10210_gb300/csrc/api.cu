@@ -551,8 +551,13 @@ int stage_inputs(efgp_handle* H, const void* x, const void* y, long long N, cons
 // of x, and later the sorting scatter of a chunk of (x, y), start as soon as
 // that chunk has arrived, so the host-to-device copy overlaps the set-up
 // (row-major x; the copies are asynchronous when the caller's memory is
-// pinned).  All x chunks are copied first, then all y chunks.
+// pinned).  The points are taken in parts of kStagePartChunks chunks, each
+// part copied x first, then y.  The spread is linear in the points, so every
+// part is counted, sorted and spread into the same extended grid on its own:
+// a part's spread runs while the next part is copied, and only the last
+// part's spread follows the last copy.
 constexpr long long kStageChunk = 1ll << 26;   // points per copy
+constexpr int kStagePartChunks = 2;             // chunks per part
 
 struct ChunkedStage {
   efgp_handle* H = nullptr;
@@ -575,6 +580,10 @@ struct ChunkedStage {
   }
   long long first(int i) const { return (long long)i * C; }
   long long count(int i) const { return std::min(C, N - first(i)); }
+  int nparts() const { return (nch + kStagePartChunks - 1) / kStagePartChunks; }
+  int part_begin(int p) const { return p * kStagePartChunks; }   // first chunk of part p
+  int part_end(int p) const { return std::min(nch, (p + 1) * kStagePartChunks); }
+  long long part_points(int p) const { return first(part_end(p) - 1) + count(part_end(p) - 1) - first(part_begin(p)); }
   const void* x_at(int i) const { return dx + (size_t)first(i) * xpt; }
   const void* y_at(int i) const { return dy + (size_t)first(i) * ypt; }
   int wait_x(int i) {
@@ -616,21 +625,23 @@ struct ChunkedStage {
     }
     const char* hx = static_cast<const char*>(x);
     const char* hy = static_cast<const char*>(y);
-    for (int i = 0; i < nch; ++i) {
-      EFGP_CK(cudaMemcpyAsync(dx + (size_t)first(i) * xpt, hx + (size_t)first(i) * xpt, (size_t)count(i) * xpt,
-                              cudaMemcpyHostToDevice, cs));
-      EFGP_CK(cudaEventRecord(ex[i], cs));
-    }
-    for (int i = 0; i < nch; ++i) {
-      EFGP_CK(cudaMemcpyAsync(dy + (size_t)first(i) * ypt, hy + (size_t)first(i) * ypt, (size_t)count(i) * ypt,
-                              cudaMemcpyHostToDevice, cs));
-      EFGP_CK(cudaEventRecord(ey[i], cs));
+    for (int p = 0; p < nparts(); ++p) {
+      for (int i = part_begin(p); i < part_end(p); ++i) {
+        EFGP_CK(cudaMemcpyAsync(dx + (size_t)first(i) * xpt, hx + (size_t)first(i) * xpt, (size_t)count(i) * xpt,
+                                cudaMemcpyHostToDevice, cs));
+        EFGP_CK(cudaEventRecord(ex[i], cs));
+      }
+      for (int i = part_begin(p); i < part_end(p); ++i) {
+        EFGP_CK(cudaMemcpyAsync(dy + (size_t)first(i) * ypt, hy + (size_t)first(i) * ypt, (size_t)count(i) * ypt,
+                                cudaMemcpyHostToDevice, cs));
+        EFGP_CK(cudaEventRecord(ey[i], cs));
+      }
     }
     return EFGP_OK;
   }
   int wait_all() {
+    for (int i = 0; i < nch; ++i) EFGP_TRY(wait_x(i));
     for (int i = 0; i < nch; ++i) EFGP_TRY(wait_y(i));
-    if (nch) EFGP_TRY(wait_x(nch - 1));
     return EFGP_OK;
   }
 };
@@ -785,9 +796,6 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   const int soa = H->opt.x_layout == 1;
   const size_t recb = sf64 ? 8 : 4;
   sg.x_vec = (reinterpret_cast<uintptr_t>(dx) % 8) == 0;
-  // record arrays padded to 16-byte multiples with slack after the end, so
-  // that aligned bulk-copy windows never leave the allocation
-  sg.rstride = ((N + 3) / 4) * 4 + 4;
 
   EFGP_CK(cudaMemsetAsync(H->flag, 0, 4 * sizeof(int), H->stream));
   void* P = nullptr;
@@ -810,42 +818,61 @@ int setup_device(efgp_handle* H, const void* x, const void* y) {
   EFGP_CK(cudaMemsetAsync(E, 0, sizeof(double2) * nE_tot, H->stream));
 
   if (N > 0) {
+    // host inputs: one count -> scan -> scatter -> spread pass per part of
+    // the chunks (the records buffer holds the largest part); device inputs:
+    // one pass over all N points.  (With several parts the phase marks time
+    // the last part.)
+    const int nparts = chunked ? cst.nparts() : 1;
+    long long Nmax = N;
+    if (chunked) {
+      Nmax = 0;
+      for (int p = 0; p < nparts; ++p) Nmax = std::max(Nmax, cst.part_points(p));
+    }
+    // record arrays padded to 16-byte multiples with slack after the end, so
+    // that aligned bulk-copy windows never leave the allocation
+    sg.rstride = ((Nmax + 3) / 4) * 4 + 4;
     EFGP_CK(cudaMallocAsync(&rec, recb * (size_t)sg.rstride * (d + 1), H->stream));
     temps.push_back(rec);
-    H->mark(0);
-    // tile totals, chunk by chunk as the chunks of x arrive (host inputs)
-    const int nparts = chunked ? cst.nch : 1;
-    for (int i = 0; i < nparts; ++i) {
-      const void* xi = chunked ? cst.x_at(i) : dx;
-      const long long ni = chunked ? cst.count(i) : N;
-      if (chunked) EFGP_TRY(cst.wait_x(i));
-      if (d == 2 && !coord_f64 && !sf64 && !soa && reinterpret_cast<uintptr_t>(xi) % 16 == 0 &&
-          sg.ntiles <= kFusedMaxTiles)
-        EFGP_CK(launch_tile_totals_2d((const float*)xi, ni, sg, (unsigned int*)counts, H->flag, H->stream));
-      else
-        EFGP_CK(launch_bin_count(xi, coord_f64, (int)sf64, soa, ni, sg, (unsigned int*)counts, H->flag, H->stream));
-    }
-    H->mark(1);
-    EFGP_CK(cudaMemcpyAsync(H->host_flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
-    EFGP_CK(cudaStreamSynchronize(H->stream));
-    if (*H->host_flag) {
-      set_error("a coordinate lies outside [0,1] or is not finite");
-      return EFGP_ERANGE;
-    }
-    H->mark(2);
-    EFGP_CK(launch_scan_tiles((unsigned int*)counts, sg.ntiles, (long long*)toff, (long long*)cursor, H->stream));
-    // sorting scatter (global tile cursors: chunks may go in any order), chunk
-    // by chunk as the chunks of y arrive (host inputs)
-    for (int i = 0; i < nparts; ++i) {
-      if (chunked) EFGP_TRY(cst.wait_y(i));
-      EFGP_CK(launch_bin_scatter(chunked ? cst.x_at(i) : dx, coord_f64, chunked ? cst.y_at(i) : dy, value_f64, soa,
-                                 chunked ? cst.count(i) : N, sg, (int)sf64, (long long*)cursor, rec, H->flag + 1,
-                                 H->stream));
-    }
-    H->mark(3);
     const void* coef = sf64 ? (const void*)&H->c1d : (const void*)&H->c1f;
-    EFGP_CK(launch_spread(rec, (int)sf64, N, sg, (const long long*)toff, coef, (double2*)E, H->flag + 1, H->stream));
-    H->times.launches += 2 * nparts + 2;
+    for (int p = 0; p < nparts; ++p) {
+      const int c0 = chunked ? cst.part_begin(p) : 0;
+      const int c1 = chunked ? cst.part_end(p) : 1;
+      const long long Np = chunked ? cst.part_points(p) : N;
+      if (p > 0) EFGP_CK(cudaMemsetAsync(counts, 0, sizeof(unsigned int) * sg.ntiles, H->stream));
+      H->mark(0);
+      // tile totals, chunk by chunk as the chunks of x arrive (host inputs)
+      for (int i = c0; i < c1; ++i) {
+        const void* xi = chunked ? cst.x_at(i) : dx;
+        const long long ni = chunked ? cst.count(i) : N;
+        if (chunked) EFGP_TRY(cst.wait_x(i));
+        if (d == 2 && !coord_f64 && !sf64 && !soa && reinterpret_cast<uintptr_t>(xi) % 16 == 0 &&
+            sg.ntiles <= kFusedMaxTiles)
+          EFGP_CK(launch_tile_totals_2d((const float*)xi, ni, sg, (unsigned int*)counts, H->flag, H->stream));
+        else
+          EFGP_CK(launch_bin_count(xi, coord_f64, (int)sf64, soa, ni, sg, (unsigned int*)counts, H->flag, H->stream));
+      }
+      H->mark(1);
+      EFGP_CK(cudaMemcpyAsync(H->host_flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, H->stream));
+      EFGP_CK(cudaStreamSynchronize(H->stream));
+      if (*H->host_flag) {
+        set_error("a coordinate lies outside [0,1] or is not finite");
+        return EFGP_ERANGE;
+      }
+      H->mark(2);
+      EFGP_CK(launch_scan_tiles((unsigned int*)counts, sg.ntiles, (long long*)toff, (long long*)cursor, H->stream));
+      // sorting scatter (global tile cursors: chunks may go in any order),
+      // chunk by chunk as the chunks of y arrive (host inputs)
+      for (int i = c0; i < c1; ++i) {
+        if (chunked) EFGP_TRY(cst.wait_y(i));
+        EFGP_CK(launch_bin_scatter(chunked ? cst.x_at(i) : dx, coord_f64, chunked ? cst.y_at(i) : dy, value_f64,
+                                   soa, chunked ? cst.count(i) : N, sg, (int)sf64, (long long*)cursor, rec,
+                                   H->flag + 1, H->stream));
+      }
+      H->mark(3);
+      EFGP_CK(launch_spread(rec, (int)sf64, Np, sg, (const long long*)toff, coef, (double2*)E, H->flag + 1,
+                            H->stream));
+      H->times.launches += 2 * (c1 - c0) + 2;
+    }
   }
   H->mark(4);
 

@@ -842,56 +842,56 @@ __global__ void __launch_bounds__(kRegThreads, 2) spread_reg_kernel(const float*
 }
 
 
-// Register-accumulating spread fed by bulk asynchronous copies (FP32
-// records, d = 1 or 2).  The sorted records of a block's segment are walked
-// as a sequence of batches (tile, first point, count); each batch's
-// coordinate and value runs are copied into one of two shared staging
-// buffers while the previous batch is processed.  A batch is counting-sorted
-// by fine cell through a 16-bit index array; two threads own each of the 256
-// cells of a tile and split the cell's points, each adding W^d weights into
-// registers.  The registers of a tile visit are added into a shared tile in
-// conflict-free phases and the tile is flushed to the FP64 grid.  The record
-// arrays are padded so that 16-byte aligned copy windows stay in bounds.
-constexpr int kTmaSpreadThreads = 512;
-constexpr int kTmaSpreadBatch = 8192;
-constexpr int kTmaSpreadSlot = kTmaSpreadBatch + 8;   // floats per staged array
 constexpr int kSpreadUnroll = 2;   // points of a cell whose weights are evaluated together (4: no gain)
 
+// Register-accumulating spread with two resident blocks per SM (FP32
+// records, d = 1 or 2).  One thread owns each of the 256 cells of a tile.
+// A batch of the tile-sorted records is copied into a staging buffer by one
+// bulk asynchronous copy per array, counted by fine cell, and reordered by
+// cell into a second buffer (coordinates, value); the staging buffer
+// is then free, so the copy of the next batch lands while the threads walk
+// their cells' runs from contiguous shared memory.  The two blocks of an SM
+// interleave: the sorting phases and barrier waits of one overlap the
+// multiply-adds of the other.
+constexpr int kPairThreads = 256;
+constexpr int kPairBatch = 4096;
+constexpr int kPairSlot = kPairBatch + 8;   // floats per staged array
+
 template <int D, int W>
-__global__ void __launch_bounds__(kTmaSpreadThreads, 1)
-    spread_tma_kernel(const float* __restrict__ rec, long long N, long long rstride, SortGeom sg,
-                      const long long* __restrict__ tile_off, long long seg_len, EsCoef<float> cf,
-                      double2* __restrict__ E, int* err) {
+__global__ void __launch_bounds__(kPairThreads, 2)
+    spread_pair_kernel(const float* __restrict__ rec, long long N, long long rstride, SortGeom sg,
+                       const long long* __restrict__ tile_off, long long seg_len, EsCoef<float> cf,
+                       double2* __restrict__ E, int* err) {
   constexpr int TB = RegTile<D>::TB;
   constexpr int S = TB + W - 1;
   constexpr int CELLS = (D == 1) ? S : S * S;
   constexpr int FP = (D == 1) ? W : W * W;
-  constexpr int NT = kTmaSpreadThreads;
-  constexpr int B = kTmaSpreadBatch;
-  constexpr int SLOT = kTmaSpreadSlot;
-  constexpr int NA = D + 1;   // staged arrays per batch
+  constexpr int NT = kPairThreads;
+  constexpr int B = kPairBatch;
+  constexpr int SLOT = kPairSlot;
+  constexpr int NA = D + 1;   // arrays per record: D coordinates, one value
+  static_assert(NT == 256, "one thread per cell of a 256-cell tile");
   extern __shared__ __align__(128) unsigned char smraw[];
-  float* stage = reinterpret_cast<float*>(smraw);                 // 2 * NA * SLOT
-  float* tile = stage + 2 * NA * SLOT;                             // 2 * CELLS
-  unsigned short* idx = reinterpret_cast<unsigned short*>(tile + 2 * CELLS);  // B
-  int* cnt = reinterpret_cast<int*>(idx + B);                      // 256
-  int* cur = cnt + 256;                                            // 256
-  unsigned char* ucell = reinterpret_cast<unsigned char*>(cur + 256);   // B: each point's cell
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int wtot[8];
-  __shared__ int it_tile[2], it_off[2];
+  float* stage = reinterpret_cast<float*>(smraw);                  // NA * SLOT
+  float* sorted = stage + NA * SLOT;                                // NA * B
+  float* tile = sorted + NA * B;                                    // 2 * CELLS
+  int* cnt = reinterpret_cast<int*>(tile + 2 * CELLS);              // 256
+  int* cur = cnt + 256;                                             // 256
+  unsigned char* ucell = reinterpret_cast<unsigned char*>(cur + 256);   // B
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int wtot[32];
+  __shared__ int it_tile[2], it_n[2];
   __shared__ long long it_p0[2];
-  __shared__ int it_n[2];
+  __shared__ int it_off;
   __shared__ int abort_flag;
   const int t = threadIdx.x;
-  const int cell = t & 255, half = t >> 8;
   const long long s0 = blockIdx.x * seg_len;
   const long long s1 = min(N, s0 + seg_len);
   if (s0 >= s1) return;
 
-  // next batch after (tile tt, start p0): returns false at the segment end
+  // next batch after (tile tt, start p0, count n): false at the segment end
   auto next_item = [&](int& tt, long long& p0, int& n) -> bool {
-    long long b = min(s1, tile_off[tt + 1]);
+    const long long b = min(s1, tile_off[tt + 1]);
     p0 += n;
     if (p0 < b) {
       n = (int)min((long long)B, b - p0);
@@ -909,20 +909,19 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
     }
     return false;
   };
-  // copy the batch's arrays into staging buffer `slot`
-  auto issue = [&](int slot, long long p0, int n) {
+  // copy the batch's arrays into the staging buffer: a window of whole
+  // 16-byte groups, (p0 + n + 3) & ~3 <= rstride - 4 keeps it in bounds
+  auto issue = [&](long long p0, int n) {
     const long long pa = p0 & ~3ll;
     const long long pe = (p0 + n + 3) & ~3ll;
     const uint32_t bytes = (uint32_t)((pe - pa) * 4);
-    mbar_arrive_expect_tx(&bar[slot], bytes * NA);
-    for (int a = 0; a < NA; ++a)
-      bulk_g2s(stage + (slot * NA + a) * SLOT, rec + a * rstride + pa, bytes, &bar[slot]);
-    it_off[slot] = (int)(p0 - pa);
+    mbar_arrive_expect_tx(&bar, bytes * NA);
+    for (int a = 0; a < NA; ++a) bulk_g2s(stage + a * SLOT, rec + a * rstride + pa, bytes, &bar);
+    it_off = (int)(p0 - pa);
   };
 
   if (t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(&bar, 1);
     fence_barrier_init();
     abort_flag = 0;
     int lo = 0, hi = sg.ntiles - 1;
@@ -930,31 +929,27 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
       const int mid = (lo + hi + 1) >> 1;
       if (tile_off[mid] <= s0) lo = mid; else hi = mid - 1;
     }
-    // first batch: the tile holding s0 (tiles before it may be empty)
     int tt = lo;
     long long p0 = s0;
     int n = 0;
     bool ok;
-    {
-      const long long b = min(s1, tile_off[tt + 1]);
-      if (p0 < b) {
-        n = (int)min((long long)B, b - p0);
-        ok = true;
-      } else {
-        n = 0;
-        ok = next_item(tt, p0, n);
-      }
+    const long long b = min(s1, tile_off[tt + 1]);
+    if (p0 < b) {
+      n = (int)min((long long)B, b - p0);
+      ok = true;
+    } else {
+      ok = next_item(tt, p0, n);
     }
     it_tile[0] = ok ? tt : -1;
     it_p0[0] = p0;
     it_n[0] = n;
-    if (ok) issue(0, p0, n);
+    if (ok) issue(p0, n);
   }
   __syncthreads();
 
   int own[D];
   {
-    int r = cell;
+    int r = t;
 #pragma unroll
     for (int a = D - 1; a >= 0; --a) {
       own[a] = r % TB;
@@ -964,36 +959,32 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
   float2 acc[FP];   // (strength 1, strength y) per footprint cell
 #pragma unroll
   for (int i = 0; i < FP; ++i) acc[i] = make_float2(0.f, 0.f);
+  // by cell: the coordinates (a float2 per point in 2D) and the values
+  float* q1s = sorted;                                      // d = 1
+  float2* q2s = reinterpret_cast<float2*>(sorted);          // d = 2
+  float* ys = sorted + D * B;
+  float ownf[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) ownf[a] = (float)own[a];
 
   int abort_it = -1;
   for (int it = 0;; ++it) {
     const int b = it & 1;
     const int tt = it_tile[b];
     if (tt < 0) break;
-    const long long p0 = it_p0[b];
     const int n = it_n[b];
-    if (t == 0) {
-      int nt = tt;
-      long long np0 = p0;
-      int nn = n;
-      const bool ok = next_item(nt, np0, nn);
-      it_tile[b ^ 1] = ok ? nt : -1;
-      it_p0[b ^ 1] = np0;
-      it_n[b ^ 1] = nn;
-      if (ok) issue(b ^ 1, np0, nn);
-    }
-    if (!mbar_wait_bounded(&bar[b], (uint32_t)((it >> 1) & 1), err)) abort_flag = 1;
-    if (t < 256) cnt[t] = 0;
+    if (!mbar_wait_bounded(&bar, (uint32_t)(it & 1), err)) abort_flag = 1;
+    cnt[t] = 0;
     __syncthreads();
     if (abort_flag) {
       abort_it = it;
       break;
     }
-    const int off = it_off[b];
-    const float* sq0 = stage + (b * NA) * SLOT + off;
-    const float* sq1 = stage + (b * NA + (D - 1)) * SLOT + off;
-    const float* sy = stage + (b * NA + D) * SLOT + off;
-    // count by cell (the cell is kept for the index pass)
+    const int off = it_off;
+    const float* sq0 = stage + off;
+    const float* sq1 = stage + (D - 1) * SLOT + off;
+    const float* sy = stage + D * SLOT + off;
+    // count by cell (the cell is kept for the reorder)
     for (int k = t; k < n; k += NT) {
       float q[D], f[D];
       q[0] = sq0[k];
@@ -1003,47 +994,31 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
       atomicAdd(&cnt[c], 1);
     }
     __syncthreads();
-    int mine = 0, st = 0;
-    if (t < 256) {
-      mine = cnt[t];
-    }
-    // exclusive scan over the 256 cells by the first 256 threads
-    {
-      const int lane = t & 31, wid = t >> 5;
-      int x = mine;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (wid < 8 && lane == 31) wtot[wid] = x;
-      __syncthreads();
-      if (wid == 0) {
-        int w = lane < 8 ? wtot[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, w, o);
-          if (lane >= o) w += y;
-        }
-        if (lane < 8) wtot[lane] = w;
-      }
-      __syncthreads();
-      if (t < 256) {
-        st = (wid > 0 ? wtot[wid - 1] : 0) + x - mine;
-        cur[t] = st;
-      }
-    }
+    const int mine = cnt[t];
+    const int start = block_excl_scan_n<NT>(mine, wtot);
+    cur[t] = start;
     __syncthreads();
+    // reorder by cell
     for (int k = t; k < n; k += NT) {
       const int pos = atomicAdd(&cur[ucell[k]], 1);
-      idx[pos] = (unsigned short)k;
+      if (D == 2) q2s[pos] = make_float2(sq0[k], sq1[k]);
+      else q1s[pos] = sq0[k];
+      ys[pos] = sy[k];
     }
     __syncthreads();
-    // run of my cell: start = cur[cell] - cnt[cell] after the index pass;
-    // points taken two at a time (independent weight evaluations interleave)
+    // the staging buffer is free: start the copy of the next batch
+    if (t == 0) {
+      int nt = tt;
+      long long np0 = it_p0[b];
+      int nn = n;
+      const bool ok = next_item(nt, np0, nn);
+      it_tile[b ^ 1] = ok ? nt : -1;
+      it_p0[b ^ 1] = np0;
+      it_n[b ^ 1] = nn;
+      if (ok) issue(np0, nn);
+    }
+    // the run of my cell, two points per step (independent weight chains)
     {
-      const int c_n = cnt[cell];
-      const int c_s = cur[cell] - c_n;
       auto add_point = [&](const float (&w0)[W], const float (&w1)[W], float yv) {
         const float2 c2 = make_float2(1.f, yv);
         if (D == 1) {
@@ -1058,49 +1033,50 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
           }
         }
       };
+      // in-cell offsets f = q - (cell corner), as the cell binning takes them
+      auto weights = [&](int j, float (&w0)[W], float (&w1)[W]) {
+        if (D == 2) {
+          const float2 qq = q2s[start + j];
+          es_weights_x2<W>(qq.x - ownf[0], cf, w0);
+          es_weights_x2<W>(qq.y - ownf[D - 1], cf, w1);
+        } else {
+          es_weights_x2<W>(q1s[start + j] - ownf[0], cf, w0);
+        }
+      };
+      const float* pys = ys + start;
       constexpr int UP = kSpreadUnroll;
-      int j = half;
-      for (; j + 2 * (UP - 1) < c_n; j += 2 * UP) {
-        int kk[UP];
-        float w0[UP][W], w1[UP][W];
+      int j = 0;
+      for (; j + UP - 1 < mine; j += UP) {
+        float w0[UP][W], w1[UP][W], yv[UP];
 #pragma unroll
         for (int e = 0; e < UP; ++e) {
-          kk[e] = idx[c_s + j + 2 * e];
-          es_weights_x2<W>(sq0[kk[e]] - (float)own[0], cf, w0[e]);
-          if (D == 2) es_weights_x2<W>(sq1[kk[e]] - (float)own[D - 1], cf, w1[e]);
+          weights(j + e, w0[e], w1[e]);
+          yv[e] = pys[j + e];
         }
 #pragma unroll
-        for (int e = 0; e < UP; ++e) add_point(w0[e], w1[e], sy[kk[e]]);
+        for (int e = 0; e < UP; ++e) add_point(w0[e], w1[e], yv[e]);
       }
-      for (; j < c_n; j += 2) {
-        const int k = idx[c_s + j];
+      for (; j < mine; ++j) {
         float w0[W], w1[W];
-        es_weights_x2<W>(sq0[k] - (float)own[0], cf, w0);
-        if (D == 2) es_weights_x2<W>(sq1[k] - (float)own[D - 1], cf, w1);
-        add_point(w0, w1, sy[k]);
+        weights(j, w0, w1);
+        add_point(w0, w1, pys[j]);
       }
     }
     __syncthreads();
     // last batch of this tile visit: registers -> shared tile -> FP64 grid
-    const int ntile = it_tile[b ^ 1];
-    if (ntile != tt) {
+    if (it_tile[b ^ 1] != tt) {
       for (int c = t; c < 2 * CELLS; c += NT) tile[c] = 0.f;
       __syncthreads();
-      for (int h = 0; h < 2; ++h) {
 #pragma unroll
-        for (int i = 0; i < FP; ++i) {
-          if (half == h) {
-            int cc;
-            if (D == 1) cc = own[0] + i;
-            else cc = (own[0] + i / W) * S + own[D - 1] + i % W;
-            tile[2 * cc] += acc[i].x;
-            tile[2 * cc + 1] += acc[i].y;
-          }
-          __syncthreads();
-        }
+      for (int i = 0; i < FP; ++i) {
+        int cc;
+        if (D == 1) cc = own[0] + i;
+        else cc = (own[0] + i / W) * S + own[D - 1] + i % W;
+        tile[2 * cc] += acc[i].x;
+        tile[2 * cc + 1] += acc[i].y;
+        acc[i] = make_float2(0.f, 0.f);
+        __syncthreads();
       }
-#pragma unroll
-      for (int i = 0; i < FP; ++i) acc[i] = make_float2(0.f, 0.f);
       int tcv[2] = {0, 0};
       {
         int r = tt;
@@ -1130,18 +1106,17 @@ __global__ void __launch_bounds__(kTmaSpreadThreads, 1)
       __syncthreads();
     }
   }
-  // after an abandoned wait, let the copy already issued into the other
-  // buffer land (bounded) before the block's shared memory is released
-  if (abort_flag && t == 0 && abort_it >= 0 && it_tile[(abort_it & 1) ^ 1] >= 0)
-    mbar_wait_bounded(&bar[(abort_it & 1) ^ 1], (uint32_t)(((abort_it + 1) >> 1) & 1), nullptr);
+  // after an abandoned wait, let the copy already issued land (bounded)
+  // before the block's shared memory is released
+  if (abort_it >= 0 && t == 0) mbar_wait_bounded(&bar, (uint32_t)(abort_it & 1), nullptr);
 }
 
-size_t spread_tma_smem(int d, int W) {
+size_t spread_pair_smem(int d, int W) {
   const int TB = d == 1 ? RegTile<1>::TB : RegTile<2>::TB;
   const int S = TB + W - 1;
   const int cells = d == 1 ? S : S * S;
-  return sizeof(float) * (2 * (size_t)(d + 1) * kTmaSpreadSlot + 2 * cells) +
-         sizeof(unsigned short) * kTmaSpreadBatch + sizeof(int) * 512 + sizeof(unsigned char) * kTmaSpreadBatch;
+  return sizeof(float) * ((size_t)(d + 1) * (kPairSlot + kPairBatch) + 2 * cells) + sizeof(int) * 512 +
+         sizeof(unsigned char) * kPairBatch;
 }
 
 size_t spread_reg_smem(int d, int W) {
@@ -1467,18 +1442,21 @@ static cudaError_t spread_dw(const void* rec, long long N, const SortGeom& sg, c
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   constexpr bool use_tma = std::is_same<TR, float>::value && (D == 1 || (D == 2 && W <= 6));
   if constexpr (use_tma) {
-    const size_t sm = spread_tma_smem(D, W);
-    if (sg.TB == RegTile<(D == 1 ? 1 : 2)>::TB && sm <= 226 * 1024 && sg.rstride % 4 == 0 &&
+    const size_t smp = spread_pair_smem(D, W);
+    if (sg.TB == RegTile<(D == 1 ? 1 : 2)>::TB && smp <= 110 * 1024 && sg.rstride % 4 == 0 &&
         reinterpret_cast<uintptr_t>(rec) % 16 == 0) {
-      auto k = spread_tma_kernel<(D == 1 ? 1 : 2), W>;
-      cudaError_t e = allow_smem(k, sm);
+      auto k = spread_pair_kernel<(D == 1 ? 1 : 2), W>;
+      cudaError_t e = allow_smem(k, smp);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
       if (e != cudaSuccess) return e;
-      long long nseg = (long long)nsm * 4;
+      // two resident blocks per SM, about four waves of equal segments
+      long long nseg = (long long)nsm * 2 * 4;
       long long seg = (N + nseg - 1) / nseg;
-      if (seg < kTmaSpreadBatch) seg = kTmaSpreadBatch;
+      if (seg < kPairBatch) seg = kPairBatch;
       nseg = (N + seg - 1) / seg;
-      k<<<(unsigned)nseg, kTmaSpreadThreads, sm, s>>>(reinterpret_cast<const float*>(rec), N, sg.rstride, sg, tile_off,
-                                                       seg, *reinterpret_cast<const EsCoef<float>*>(coef), E, err);
+      k<<<(unsigned)nseg, kPairThreads, smp, s>>>(reinterpret_cast<const float*>(rec), N, sg.rstride, sg, tile_off,
+                                                  seg, *reinterpret_cast<const EsCoef<float>*>(coef), E, err);
       return cudaGetLastError();
     }
   }
