@@ -650,10 +650,23 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             samples.append(time.perf_counter() - t0)
         te = max_over_ranks(statistics.median(samples), dist, dev)
+        # the host link alone: the same pinned x and y copied to the device
+        # (same values) with nothing else running, median of three
+        copies = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x.copy_(xh, non_blocking=True)
+            y.copy_(yh, non_blocking=True)
+            torch.cuda.synchronize()
+            copies.append(time.perf_counter() - t0)
+        tc = statistics.median(copies)
         e2e = {"value": job_throughput(rec.n, world, 1000 * te), "unit": UNIT,
                "h2d_bytes_per_step": int(xn.nbytes + yn.nbytes + zn.nbytes), "d2h_bytes_per_step": int(mu_h.nbytes),
                "ms_per_step": 1000 * te, "statistic": "median of %d steps" % ke,
-               "mean_ms": 1000 * statistics.mean(samples), "samples_ms": [round(1000 * v, 2) for v in samples]}
+               "mean_ms": 1000 * statistics.mean(samples), "samples_ms": [round(1000 * v, 2) for v in samples],
+               "h2d_copy_ms": 1000 * tc, "h2d_link_gbs": (xh.nbytes + yh.nbytes) / tc / 1e9,
+               "over_copy": te / tc}
 
     accuracy = None
     # other forms of the same step, outside the timed region: the bitwise
